@@ -1,0 +1,224 @@
+"""CPU oracle for the displace + render path (test infrastructure only).
+
+Only tests/, the smoke check and the bench's CPU-baseline leg may import this
+package.  The product library never calls it; it shares no code with the CUDA
+path.  The arithmetic lives in mmr_oracle.c (plain single-threaded C); this
+module only marshals numpy arrays into it.  Each function cites the part of
+the paper it follows (Mimir, arXiv 2504.20937).
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+_lib = C.CDLL(_build.build())
+
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+
+
+def _sig(name, res, *args):
+    fn = getattr(_lib, name)
+    fn.restype = res
+    fn.argtypes = list(args)
+    return fn
+
+
+_sig("orc_philox4x32_10", None, _u32p, _u32p, _u32p)
+_sig("orc_displace_f32", None, _f32p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_float)
+_sig("orc_displace_ids_f32", None, _f32p, _u32p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+     C.c_float)
+_sig("orc_displace_f64", None, _f64p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_double)
+_sig("orc_displace_h16", None, _u16p, C.c_int, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+     C.c_float)
+_sig("orc_f32_to_f16_array", None, _f32p, _u16p, C.c_uint64)
+_sig("orc_f16_to_f32_array", None, _u16p, _f32p, C.c_uint64)
+_sig("orc_f32_to_bf16_array", None, _f32p, _u16p, C.c_uint64)
+_sig("orc_bf16_to_f32_array", None, _u16p, _f32p, C.c_uint64)
+_sig("orc_camera_f64", None, _f64p, _f64p, _f64p, C.c_double, C.c_double, C.c_double, C.c_double,
+     _f64p)
+_sig("orc_camera_f32", None, _f64p, _f64p, _f64p, C.c_double, C.c_double, C.c_double, C.c_double,
+     _f32p)
+_sig("orc_project_many_f32", None, _f32p, _f32p, C.c_uint64, C.c_int, C.c_int, C.c_float, C.c_float,
+     _u32p, _f32p, C.c_void_p)
+_sig("orc_project_many_f64", None, _f64p, _f64p, C.c_uint64, C.c_double, C.c_double, _f64p, _f64p,
+     _i32p)
+_sig("orc_splat_f32", None, _f32p, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_float, C.c_float,
+     C.c_uint32, _u64p)
+_sig("orc_splat_h16", None, _u16p, C.c_int, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_float, C.c_float,
+     C.c_uint32, _u64p)
+_sig("orc_resolve", None, _u64p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_uint32, _u32p)
+
+EMPTY_KEY = np.uint64(0xFFFFFFFFFFFFFFFF)
+KIND = {"f16": 1, "bf16": 2}
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of one counter (Salmon et al., SC'11)."""
+    out = np.zeros(4, np.uint32)
+    _lib.orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def displace_f32(pos, seed, cloud, step, a):
+    """One Brownian step in FP32, in place on float32[n,3] (Sec. 4.1)."""
+    assert pos.dtype == np.float32 and pos.flags.c_contiguous
+    _lib.orc_displace_f32(pos.reshape(-1), pos.shape[0], seed, cloud, step, a)
+
+
+def displace_ids_f32(pos, ids, seed, cloud, step, a):
+    """One FP32 step for the listed point ids only (pos[j] belongs to ids[j])."""
+    ids = np.ascontiguousarray(ids, np.uint32)
+    _lib.orc_displace_ids_f32(pos.reshape(-1), ids, ids.size, seed, cloud, step, a)
+
+
+def displace_f64(pos, seed, cloud, step, a):
+    """The FP64 twin of displace_f32 (same draws, double arithmetic)."""
+    assert pos.dtype == np.float64 and pos.flags.c_contiguous
+    _lib.orc_displace_f64(pos.reshape(-1), pos.shape[0], seed, cloud, step, a)
+
+
+def displace_h16(pos_bits, kind, seed, cloud, step, a):
+    """One step with binary16 ('f16') or bfloat16 ('bf16') storage, FP32 compute."""
+    assert pos_bits.dtype == np.uint16 and pos_bits.flags.c_contiguous
+    _lib.orc_displace_h16(pos_bits.reshape(-1), KIND[kind], pos_bits.shape[0], seed, cloud, step, a)
+
+
+def f32_to_f16(x):
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.empty(x.shape, np.uint16)
+    _lib.orc_f32_to_f16_array(x.reshape(-1), out.reshape(-1), x.size)
+    return out
+
+
+def f16_to_f32(h):
+    h = np.ascontiguousarray(h, np.uint16)
+    out = np.empty(h.shape, np.float32)
+    _lib.orc_f16_to_f32_array(h.reshape(-1), out.reshape(-1), h.size)
+    return out
+
+
+def f32_to_bf16(x):
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.empty(x.shape, np.uint16)
+    _lib.orc_f32_to_bf16_array(x.reshape(-1), out.reshape(-1), x.size)
+    return out
+
+
+def bf16_to_f32(h):
+    h = np.ascontiguousarray(h, np.uint16)
+    out = np.empty(h.shape, np.float32)
+    _lib.orc_bf16_to_f32_array(h.reshape(-1), out.reshape(-1), h.size)
+    return out
+
+
+def to_storage(pos_f32, dtype):
+    """FP32 positions -> the storage encoding of `dtype` ('f32', 'f16', 'bf16')."""
+    if dtype == "f32":
+        return np.ascontiguousarray(pos_f32, np.float32).copy()
+    return (f32_to_f16 if dtype == "f16" else f32_to_bf16)(pos_f32)
+
+
+def from_storage(pos_bits, dtype):
+    if dtype == "f32":
+        return np.asarray(pos_bits, np.float32)
+    return (f16_to_f32 if dtype == "f16" else bf16_to_f32)(pos_bits)
+
+
+def displace(pos, dtype, seed, cloud, step, a):
+    """One step in the given storage dtype, in place."""
+    if dtype == "f32":
+        displace_f32(pos, seed, cloud, step, a)
+    else:
+        displace_h16(pos, dtype, seed, cloud, step, a)
+
+
+def camera_f64(eye, target, up, fovy_deg, aspect, znear, zfar):
+    """Look-at times perspective in FP64, row-major 4x4."""
+    M = np.zeros(16, np.float64)
+    _lib.orc_camera_f64(np.asarray(eye, np.float64), np.asarray(target, np.float64),
+                        np.asarray(up, np.float64), fovy_deg, aspect, znear, zfar, M)
+    return M.reshape(4, 4)
+
+
+def camera_f32(eye, target, up, fovy_deg, aspect, znear, zfar):
+    """camera_f64 rounded once to FP32."""
+    M = np.zeros(16, np.float32)
+    _lib.orc_camera_f32(np.asarray(eye, np.float64), np.asarray(target, np.float64),
+                        np.asarray(up, np.float64), fovy_deg, aspect, znear, zfar, M)
+    return M.reshape(4, 4)
+
+
+def project_f32(M32, pos, W, H, znear, zfar, want_ndc=False):
+    """FP32 projection of float32[n,3]; px = 0xffffffff when culled/off-frame."""
+    pos = np.ascontiguousarray(pos, np.float32)
+    n = pos.shape[0]
+    px = np.empty(n, np.uint32)
+    w = np.empty(n, np.float32)
+    ndc = np.zeros((n, 2), np.float32) if want_ndc else None
+    _lib.orc_project_many_f32(np.ascontiguousarray(M32, np.float32).reshape(-1), pos.reshape(-1), n,
+                              W, H, znear, zfar, px, w,
+                              ndc.ctypes.data if want_ndc else None)
+    return (px, w, ndc) if want_ndc else (px, w)
+
+
+def project_f64(M64, pos, znear, zfar):
+    pos = np.ascontiguousarray(pos, np.float64)
+    n = pos.shape[0]
+    ndc = np.zeros((n, 2), np.float64)
+    w = np.zeros(n, np.float64)
+    valid = np.zeros(n, np.int32)
+    _lib.orc_project_many_f64(np.ascontiguousarray(M64, np.float64).reshape(-1), pos.reshape(-1), n,
+                              znear, zfar, ndc, w, valid)
+    return ndc, w, valid.astype(bool)
+
+
+def empty_keys(W, H):
+    return np.full(W * H, EMPTY_KEY, np.uint64)
+
+
+def splat(pos, dtype, M32, W, H, znear, zfar, keybuf, id_base=0):
+    """Per-pixel min of bits(w) << 32 | id into keybuf (uint64[W*H])."""
+    M = np.ascontiguousarray(M32, np.float32).reshape(-1)
+    if dtype == "f32":
+        _lib.orc_splat_f32(np.ascontiguousarray(pos, np.float32).reshape(-1), pos.shape[0], M, W, H,
+                           znear, zfar, id_base, keybuf)
+    else:
+        _lib.orc_splat_h16(np.ascontiguousarray(pos, np.uint16).reshape(-1), KIND[dtype], pos.shape[0],
+                           M, W, H, znear, zfar, id_base, keybuf)
+
+
+def resolve(keybuf, colors=None, color=0xFFFFFFFF, background=0):
+    """Key buffer -> RGBA8 (uint32 per pixel)."""
+    rgba = np.empty(keybuf.size, np.uint32)
+    cptr = None
+    if colors is not None:
+        colors = np.ascontiguousarray(colors, np.uint32)
+        cptr = colors.ctypes.data
+    _lib.orc_resolve(keybuf, keybuf.size, cptr, color, background, rgba)
+    return rgba
+
+
+def render(pos, dtype, M32, W, H, znear, zfar, colors=None, color=0xFFFFFFFF, background=0):
+    """Clear + splat + resolve of one frame; returns (keys, rgba)."""
+    keys = empty_keys(W, H)
+    splat(pos, dtype, M32, W, H, znear, zfar, keys)
+    return keys, resolve(keys, colors, color, background)
+
+
+def run_frames(pos, dtype, seed, cloud, a, first_step, frames, cam_for_frame, W, H, znear, zfar,
+               colors=None, color=0xFFFFFFFF, background=0):
+    """`frames` displace+render frames; cam_for_frame(f) -> FP32 matrix.
+
+    Returns the keys and rgba of the last frame; pos is updated in place.
+    """
+    keys = rgba = None
+    for f in range(frames):
+        displace(pos, dtype, seed, cloud, first_step + f, a)
+        keys, rgba = render(pos, dtype, cam_for_frame(f), W, H, znear, zfar, colors, color, background)
+    return keys, rgba
