@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the zero-copy displace + render step on one B300.
+
+One step = one frame of the hot path: a fused kernel displaces every point
+(Philox-4x32 Brownian offsets), projects it and depth-splats it into the
+depth-id buffer, then a resolve kernel writes the RGBA8 framebuffer and
+clears the next depth-id buffer.  Inputs are resident in device memory when
+the timed region starts.
+
+Default workload: 2^22 FP32 points uniform in [0,1]^3, 1920x1080, camera
+orbiting the centre at 0.36 deg/frame, a = 5e-4.  L2 is flushed (a 512 MB
+write) before every timed frame; each frame is timed with CUDA events on the
+launching stream.  Also reported on the same run: the host round-trip path
+(positions device -> host -> device every frame), the end-to-end rate
+through the public API with each frame read back to host memory, and the
+64M-point 16-cluster 3840x2160 frame in FP32 / binary16 / bfloat16 storage.
+
+`--impl reference` times the CPU oracle (single-threaded C) on the same
+workload instead.  Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_20937_b300 import inputs  # noqa: E402
+
+METRIC = "points/s (displace+render)"
+FLUSH_BYTES = 512 << 20
+CENTRE = (0.5, 0.5, 0.5)
+UP = (0.0, 1.0, 0.0)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "pr1"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64M-point and round-trip legs")
+    ap.add_argument("--cpu-frames", type=int, default=60, help="oracle frames for the CPU baseline (0: skip)")
+    ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def scene_for(name, points=0):
+    import dataclasses
+    sc = inputs.C2 if name == "c2" else inputs.PR1
+    if points:
+        sc = dataclasses.replace(sc, n=points, name=f"{sc.name}_n{points}")
+    return sc
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2504_20937_b300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2504_20937_b300", "csrc", fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[2] == src:
+                return float(parts[3])
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampler run during a timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.file:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.file.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.file.name)
+        except Exception:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for name, v in zip(names, r[3:7]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        busy = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(busy or sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2504_20937_b300.api import Context
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scene_for(args.workload, args.points)
+    stored = inputs.encode(sc.positions(), "f32")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def make_ctx(dtype="f32", data=stored, scene=sc):
+        ctx = Context(scene.W, scene.H)
+        view = ctx.alloc_points(data.shape[0], dtype)
+        view.copy_(torch.from_numpy(data if dtype == "f32" else data.view(np.int16)))
+        ctx.set_sim(scene.philox_seed, 0, scene.amplitude, 0)
+        ctx.set_style(scene.color, scene.background)
+        ctx.set_timing(True)
+        torch.cuda.synchronize()
+        return ctx
+
+    def timed_frames(ctx, scene, frames, warm, do_flush, roundtrip=None):
+        """Per-frame device times (ms) of the whole step and of the point kernel."""
+        step_ms, point_ms, resolve_ms = [], [], []
+        for f in range(warm + frames):
+            ctx.set_camera(scene.eye(f), CENTRE, UP, scene.fovy_deg, scene.znear, scene.zfar)
+            if do_flush:
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if roundtrip is None:
+                ctx.step_and_render(stream)
+            else:
+                ctx.step_and_render_roundtrip(stream, pinned=roundtrip)
+            b.record(stream)
+            pk, rk = ctx.last_kernel_ms()
+            if f >= warm:
+                step_ms.append(a.elapsed_time(b))
+                point_ms.append(pk)
+                resolve_ms.append(rk)
+        return step_ms, point_ms, resolve_ms
+
+    ctx = make_ctx()
+    zero_copy_bytes = ctx.device_bytes
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        step_ms, point_ms, resolve_ms = timed_frames(ctx, sc, args.steps, args.warmup, True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    n = sc.n
+    pts_per_s = world * args.steps * n / (total_ms / 1e3)
+    hbm_gbs, peak_kind = measured_peaks()
+    bytes_point = 24 * n
+    bytes_frame = bytes_point + 20 * sc.W * sc.H
+    mean_point_ms = statistics.mean(point_ms)
+    achieved = bytes_point / (mean_point_ms / 1e3) / 1e9
+    traffic = profiled_traffic("points_kernel_f32_fused", sc.name)
+
+    out = {
+        "metric": METRIC, "value": pts_per_s, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded uniform cloud, numpy PCG64)",
+        "config": {"workload": sc.name, "points": n, "width": sc.W, "height": sc.H,
+                   "storage": "f32", "amplitude": sc.amplitude, "orbit_deg_per_frame": sc.deg_per_frame,
+                   "l2": f"flushed before every timed frame ({FLUSH_BYTES >> 20} MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "launch": "library default (256 threads, one thread per 48-byte point group)"},
+        "frames_per_s": world * args.steps / (total_ms / 1e3),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "hbm_gbs_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9,
+        "kernels_ms": {"points_fused": mean_point_ms, "resolve": statistics.mean(resolve_ms)},
+        "roofline": {"bound": "hbm", "kernel": "points_kernel<f32, displace, splat>",
+                     "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                     "traffic": traffic, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_point},
+        "gpu_launches": 2 * args.steps,
+        "wall_s_timed_region": wall,
+        "device_bytes": {"zero_copy": zero_copy_bytes},
+    }
+    clocks = clk.summary()
+    if clocks:
+        out["clocks"] = clocks
+
+    if rank == 0 and not args.no_extra:
+        # host round trip (pinned), same frames: the paper's RAM-based comparison
+        rt_frames = min(args.steps, 200)
+        rt_ms, _, _ = timed_frames(ctx, sc, rt_frames, 3, True, roundtrip=True)
+        out["device_bytes"]["roundtrip"] = ctx.device_bytes
+        out["roundtrip_pinned"] = {"points_per_s": rt_frames * n / (sum(rt_ms) / 1e3),
+                                   "frames_per_s": rt_frames / (sum(rt_ms) / 1e3),
+                                   "p50_ms": float(np.percentile(rt_ms, 50)),
+                                   "p99_ms": float(np.percentile(rt_ms, 99)), "frames": rt_frames,
+                                   "host_bytes_per_frame": 2 * 12 * n}
+        pg_ms, _, _ = timed_frames(ctx, sc, 20, 2, True, roundtrip=False)
+        out["roundtrip_pageable"] = {"points_per_s": 20 * n / (sum(pg_ms) / 1e3),
+                                     "p99_ms": float(np.percentile(pg_ms, 99)), "frames": 20}
+        out["zero_copy_vs_roundtrip_pinned"] = out["value"] / world / out["roundtrip_pinned"]["points_per_s"]
+        # end to end through the public API: camera in, frame read back to pinned host memory
+        host_rgba = torch.empty((sc.H, sc.W), dtype=torch.int32, pin_memory=True)
+        e2e_frames = min(args.steps, 300)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f in range(e2e_frames):
+            ctx.set_camera(sc.eye(f), CENTRE, UP, sc.fovy_deg, sc.znear, sc.zfar)
+            ctx.step_and_render(stream)
+            host_rgba.copy_(ctx.frame_rgba(), non_blocking=True)
+            stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+        out["e2e"] = {"value": e2e_frames * n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 64,
+                      "d2h_bytes_per_step": 4 * sc.W * sc.H, "frames": e2e_frames,
+                      "note": "camera matrix in as kernel parameters, RGBA frame copied to pinned host memory"
+                              " and synchronised every frame"}
+        ctx.close()
+        out["c3_64Mpts_gmm16_3840x2160"] = run_c3(make_ctx, timed_frames, hbm_gbs)
+    else:
+        ctx.close()
+    return out
+
+
+def run_c3(make_ctx, timed_frames, hbm_gbs, frames=20):
+    """64M-point 16-cluster Gaussian mixture at 3840x2160 (inputs larger than
+    L2, no flush needed): FP32, binary16 and bfloat16 storage."""
+    sc = inputs.C3
+    pos64 = sc.positions()
+    res = {}
+    for dtype in ("f32", "f16", "bf16"):
+        data = inputs.encode(pos64, dtype)
+        ctx = make_ctx(dtype, data, sc)
+        step_ms, point_ms, resolve_ms = timed_frames(ctx, sc, frames, 3, False)
+        ctx.close()
+        bpp = inputs.BYTES_PER_POINT[dtype] * 2
+        frame_bytes = bpp * sc.n + 20 * sc.W * sc.H
+        mean_step = statistics.mean(step_ms)
+        pk = statistics.mean(point_ms)
+        res[dtype] = {"ms_per_frame": mean_step, "frames_per_s": 1e3 / mean_step,
+                      "points_per_s": sc.n / (mean_step / 1e3),
+                      "p99_ms": float(np.percentile(step_ms, 99)),
+                      "hbm_gbs_frame": frame_bytes / (mean_step / 1e3) / 1e9,
+                      "frac_frame": frame_bytes / (mean_step / 1e3) / 1e9 / hbm_gbs,
+                      "points_kernel_ms": pk, "resolve_ms": statistics.mean(resolve_ms),
+                      "points_kernel_gbs": bpp * sc.n / (pk / 1e3) / 1e9,
+                      "points_kernel_frac": bpp * sc.n / (pk / 1e3) / 1e9 / hbm_gbs}
+        del data
+    return res
+
+
+# ---------------------------------------------------------------- reference
+
+def cpu_oracle_rate(sc, stored, frames, points):
+    """The oracle as it stands (single-threaded C) on `frames` frames of a
+    `points`-point slice of the workload, full-size framebuffer."""
+    import oracle
+    pos = stored[:points].copy()
+    t0 = time.perf_counter()
+    for f in range(frames):
+        oracle.displace_f32(pos, sc.philox_seed, 0, f, np.float32(sc.amplitude))
+        M = oracle.camera_f32(sc.eye(f), CENTRE, UP, sc.fovy_deg, sc.aspect, sc.znear, sc.zfar)
+        oracle.render(pos, "f32", M, sc.W, sc.H, np.float32(sc.znear), np.float32(sc.zfar))
+    dt = time.perf_counter() - t0
+    return frames * points / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sc = scene_for(args.workload, args.points)
+    stored = inputs.encode(sc.positions(), "f32")
+    sample = min(sc.n, 1 << 20)
+    cpu_oracle_rate(sc, stored, args.warmup, sample)     # warm-up steps, untimed
+    rate, dt = cpu_oracle_rate(sc, stored, args.steps, sample)
+    desc = (f"{args.steps} frames, each displacing and rendering the first {sample} of {sc.n} points "
+            f"into the full {sc.W}x{sc.H} frame")
+    return {"metric": METRIC, "value": rate, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": sc.name, "points": sc.n, "width": sc.W, "height": sc.H, "storage": "f32"},
+            "cpu_baseline": {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": rate, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        if args.cpu_frames > 0:
+            sc = scene_for(args.workload, args.points)
+            stored = inputs.encode(sc.positions(), "f32")
+            frames = args.cpu_frames
+            rate, dt = cpu_oracle_rate(sc, stored, frames, sc.n)
+            out["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the "
+                                             f"workload on one host core, {dt:.1f} s"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * mmr.h - C ABI of libmmr: zero-copy displace + render of a device-resident
+ * point cloud on one GPU (NVIDIA B300, sm_103a).
+ *
+ * Usage model (Mimir, Sec. 3.2.1 and Listing 1): the simulation replaces its
+ * own device allocation of the visualised data with a library call that
+ * returns a plain device pointer; the simulation writes through that pointer
+ * and the library renders from the same memory, so the data never leaves the
+ * GPU.  The paper's render thread and prepareViews/updateViews critical
+ * section (Sec. 3.4, Listing 2) become stream ordering: every call that takes
+ * a stream only enqueues work on it, and a frame is valid once that stream
+ * has been synchronised.  The paper draws through Vulkan; here projection and
+ * a depth-tested 1-px splat are CUDA kernels writing a framebuffer that stays
+ * in device memory.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named dev_* or returned as device pointers are GPU addresses of
+ *    the device that was current when mmr_create ran; host arrays are read
+ *    during the call only.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued, not finished, when the call returns.
+ *  - Calls on one context are not thread-safe; distinct contexts are
+ *    independent.
+ *  - Errors return a negative mmr_status; nothing aborts the process and no
+ *    kernel traps.  mmr_last_error(ctx) gives a message for the last failure
+ *    on that context.
+ */
+#ifndef MMR_H
+#define MMR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MMR_API __attribute__((visibility("default")))
+#else
+#define MMR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mmr_ctx mmr_ctx;
+typedef int mmr_status;
+
+enum {
+    MMR_OK = 0,
+    MMR_ERR_INVALID_ARG = -1,  /* a pointer is NULL, a size is 0 or too large, a value out of range */
+    MMR_ERR_OOM = -2,          /* a device or pinned-host allocation failed */
+    MMR_ERR_BUDGET = -3,       /* the allocation would exceed the context's device-memory budget */
+    MMR_ERR_CUDA = -4,         /* a CUDA runtime call or kernel launch failed (message has the text) */
+    MMR_ERR_STATE = -5,        /* call out of order (no points yet, no camera yet, already allocated) */
+    MMR_ERR_TIMEOUT = -6       /* reserved: a bounded device-side wait gave up */
+};
+
+/* Position storage: three packed coordinates per point (x, y, z), array of
+ * structures, as the paper's float3 position format (Listing 1).  The 16-bit
+ * forms hold binary16 or bfloat16 bit patterns; arithmetic is FP32. */
+enum mmr_dtype { MMR_F32x3 = 0, MMR_F16x3 = 1, MMR_BF16x3 = 2 };
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Create a context with a width x height framebuffer on the current device
+ * (the paper's createInstance(w, h, &instance), Listing 1).  Allocates the
+ * RGBA8 framebuffer (uint32 per pixel, row 0 at the top) and two 64-bit
+ * depth-id buffers, all cleared.  1 <= width, height <= 32768.
+ * budget_bytes: device-memory cap for everything this context allocates
+ * (0 = no cap); an allocation over it fails with MMR_ERR_BUDGET.
+ * On failure *out is NULL and nothing stays allocated. */
+MMR_API mmr_status mmr_create(int width, int height, mmr_ctx **out);
+MMR_API mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx **out);
+
+/* Release every device and host allocation of the context (the points
+ * pointer included).  Waits for work the context enqueued to finish.  A NULL
+ * ctx is a no-op.  Every pointer the context handed out is invalid after. */
+MMR_API mmr_status mmr_destroy(mmr_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none); for a NULL ctx, the last
+ * failure of mmr_create in this process.  Valid until the next call on ctx. */
+MMR_API const char *mmr_last_error(const mmr_ctx *ctx);
+MMR_API const char *mmr_status_string(mmr_status s);
+
+/* ---- data ----------------------------------------------------------------- */
+
+/* Allocate device storage for n points of the given dtype and return its
+ * device pointer (the paper's allocLinear, Sec. 3.2.1 / Table 2: same role as
+ * cudaMalloc).  The simulation writes positions through *dev_ptr; the
+ * library owns the memory: never cudaFree it.  The buffer is 256-byte aligned
+ * and zero-filled.  1 <= n < 2^32.  One point buffer per context
+ * (MMR_ERR_STATE on a second call). */
+MMR_API mmr_status mmr_alloc_points(mmr_ctx *ctx, uint64_t n, int dtype, void **dev_ptr);
+
+/* Allocate an optional per-point colour buffer (n uint32 RGBA8 values, the
+ * paper's Color property, Sec. 3.2.2) and return its device pointer.  Once
+ * allocated, resolve colours each covered pixel with colors[winning id];
+ * without it every point takes the default colour (Sec. 4.1: one colour). */
+MMR_API mmr_status mmr_alloc_colors(mmr_ctx *ctx, uint32_t **dev_colors);
+
+/* ---- view and simulation parameters --------------------------------------- */
+
+/* Camera (the paper's interactive camera, Sec. 1): right-handed look-at from
+ * eye to target with the given up vector, times an OpenGL-style perspective
+ * with vertical field of view fovy_deg and aspect width/height.  Built in FP64
+ * on the host and rounded once to FP32; a point is drawn only when
+ * znear < clip w < zfar (clip w is its distance along the view axis).
+ * Requires 0 < fovy_deg < 180, 0 < znear < zfar, eye != target. */
+MMR_API mmr_status mmr_set_camera(mmr_ctx *ctx, const double eye[3], const double target[3],
+                          const double up[3], double fovy_deg, double znear, double zfar);
+
+/* Set the FP32 row-major 4x4 clip matrix directly (rows x, y and w are used)
+ * and the depth range; mmr_get_matrix returns the matrix in use. */
+MMR_API mmr_status mmr_set_matrix(mmr_ctx *ctx, const float m[16], float znear, float zfar);
+MMR_API mmr_status mmr_get_matrix(const mmr_ctx *ctx, float m[16]);
+
+/* Displacement parameters (Sec. 4.1, Brownian motion).  Each step moves every
+ * coordinate by amplitude * (2u - 1), u the top 24 bits of a
+ * Philox4x32-10 draw with counter (point, step, cloud, 0) and key
+ * (seed low, seed high) scaled by 2^-24, then clamps it to [0, 1].  The next
+ * step index is first_step.  0 <= amplitude <= 1, finite. */
+MMR_API mmr_status mmr_set_sim(mmr_ctx *ctx, uint64_t seed, uint32_t cloud, float amplitude,
+                       uint32_t first_step);
+
+/* Default point colour (no colour buffer) and background colour, RGBA8. */
+MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background);
+
+/* Kernel launch shape: threads per block (a multiple of 32, 32..1024) and
+ * CTAs per SM for the point kernel's grid (0 = one thread per point group).
+ * Results do not depend on it; only speed does. */
+MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm);
+
+/* ---- frames ---------------------------------------------------------------- */
+
+/* One frame: displace every point (current step), project and depth-splat
+ * it (key = bits(clip w) << 32 | point id, per-pixel minimum), then resolve
+ * the keys to RGBA8.  Displacement and splat are one fused kernel; resolve
+ * also clears the other depth-id buffer for the next frame.  Advances the
+ * step counter.  Requires points and a camera. */
+MMR_API mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream);
+
+/* Displace only (advances the step counter). */
+MMR_API mmr_status mmr_displace(mmr_ctx *ctx, void *stream);
+
+/* Render only: the simulation already wrote the positions (the paper's
+ * updateViews after a user kernel, Listing 2). */
+MMR_API mmr_status mmr_render(mmr_ctx *ctx, void *stream);
+
+/* The host round-trip baseline (the paper's RAM-based comparison, abstract
+ * and Sec. 4.1): displace on the device, copy the positions device -> host
+ * (pinned when pinned_host != 0, else pageable) -> a second device buffer,
+ * then render that copy.  Output is identical to mmr_step_and_render.  The
+ * extra host and device buffers are allocated on first use and counted
+ * against the budget. */
+MMR_API mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int pinned_host);
+
+/* Device pointers of the latest frame: RGBA8 (width*height uint32) and its
+ * depth-id keys (width*height uint64, all-ones = empty).  Valid after the
+ * stream that rendered the frame is synchronised, until the next frame or
+ * mmr_destroy.  Either output pointer may be NULL. */
+MMR_API mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **depth_id);
+
+/* Current step counter (index of the next displacement step). */
+MMR_API mmr_status mmr_get_step(const mmr_ctx *ctx, uint32_t *step);
+
+/* Per-kernel timing for benchmarks.  When enabled, the library records CUDA
+ * events on the frame's stream around the point kernel and the resolve
+ * kernel of every frame; mmr_last_kernel_ms waits for the latest frame's
+ * events and returns both durations in milliseconds (either pointer may be
+ * NULL).  MMR_ERR_STATE if timing is off or no frame was timed yet. */
+MMR_API mmr_status mmr_set_timing(mmr_ctx *ctx, int enable);
+MMR_API mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *resolve_ms);
+
+/* Device bytes this context holds right now. */
+MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MMR_H */

@@ -1,0 +1,93 @@
+"""ctypes binding of libmmr (include/mmr.h): argument marshalling only.
+
+Every step of the displace + render path runs in the library's CUDA kernels.
+PyTorch is used only to hold device memory (views of library-owned buffers)
+and to supply streams.  There is no fallback: if libmmr.so is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmmr.so")
+
+MMR_OK = 0
+STATUS = {0: "MMR_OK", -1: "MMR_ERR_INVALID_ARG", -2: "MMR_ERR_OOM", -3: "MMR_ERR_BUDGET",
+          -4: "MMR_ERR_CUDA", -5: "MMR_ERR_STATE", -6: "MMR_ERR_TIMEOUT"}
+DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2}
+
+_vp = C.c_void_p
+_u64 = C.c_uint64
+_u32 = C.c_uint32
+_i = C.c_int
+_d = C.c_double
+_f = C.c_float
+_d3 = C.c_double * 3
+_f16 = C.c_float * 16
+
+# name -> (restype, argtypes); the exported surface of include/mmr.h
+SIGNATURES = {
+    "mmr_create": (_i, [_i, _i, C.POINTER(_vp)]),
+    "mmr_create_ex": (_i, [_i, _i, _u64, C.POINTER(_vp)]),
+    "mmr_destroy": (_i, [_vp]),
+    "mmr_last_error": (C.c_char_p, [_vp]),
+    "mmr_status_string": (C.c_char_p, [_i]),
+    "mmr_alloc_points": (_i, [_vp, _u64, _i, C.POINTER(_vp)]),
+    "mmr_alloc_colors": (_i, [_vp, C.POINTER(_vp)]),
+    "mmr_set_camera": (_i, [_vp, _d3, _d3, _d3, _d, _d, _d]),
+    "mmr_set_matrix": (_i, [_vp, _f16, _f, _f]),
+    "mmr_get_matrix": (_i, [_vp, _f16]),
+    "mmr_set_sim": (_i, [_vp, _u64, _u32, _f, _u32]),
+    "mmr_set_style": (_i, [_vp, _u32, _u32]),
+    "mmr_set_launch": (_i, [_vp, _i, _i]),
+    "mmr_step_and_render": (_i, [_vp, _vp]),
+    "mmr_displace": (_i, [_vp, _vp]),
+    "mmr_render": (_i, [_vp, _vp]),
+    "mmr_step_and_render_roundtrip": (_i, [_vp, _vp, _i]),
+    "mmr_frame_ptr": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
+    "mmr_get_step": (_i, [_vp, C.POINTER(_u32)]),
+    "mmr_set_timing": (_i, [_vp, _i]),
+    "mmr_last_kernel_ms": (_i, [_vp, C.POINTER(_f), C.POINTER(_f)]),
+    "mmr_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
+}
+
+_lib = None
+
+
+class MmrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def load() -> C.CDLL:
+    """Load the in-tree libmmr.so (build it with paper_2504_20937_b300/build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmmr.so not built at {LIB_PATH}; run paper_2504_20937_b300/build.py")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(status: int, ctx=None) -> None:
+    if status != MMR_OK:
+        msg = load().mmr_last_error(ctx)
+        raise MmrError(status, msg.decode() if msg else "")
+
+
+def stream_handle(stream) -> int | None:
+    """torch.cuda.Stream / raw handle / None -> cudaStream_t as an int."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None

@@ -1,0 +1,165 @@
+"""Python face of libmmr: a thin object wrapper over the C ABI.
+
+    ctx = Context(1920, 1080)
+    pos = ctx.alloc_points(n, "f32")        # torch view of library-owned device memory
+    pos.copy_(initial_positions)            # the simulation writes it directly
+    ctx.set_camera(eye, target, up, 60.0, 0.1, 100.0)
+    ctx.set_sim(seed, cloud=0, amplitude=5e-4)
+    ctx.step_and_render()                    # enqueued on torch's current stream
+    rgba = ctx.frame_rgba()                  # torch view of the device framebuffer
+
+Mirrors the paper's usage model (Mimir, Listing 1 and Table 2): the
+visualised allocation comes from the library and is written in place.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import DTYPE_CODE, MmrError, check, stream_handle
+
+_TORCH_VIEW = {"f32": (torch.float32, "<f4"), "f16": (torch.int16, "<i2"), "bf16": (torch.int16, "<i2")}
+
+
+class _DeviceArray:
+    """Minimal __cuda_array_interface__ holder for a library-owned pointer."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 2, "strides": None}
+
+
+def device_view(ptr: int, shape, typestr: str) -> torch.Tensor:
+    """A torch tensor aliasing device memory at ptr (no copy, no ownership)."""
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
+
+
+class Context:
+    """One framebuffer, one point cloud, one camera (include/mmr.h)."""
+
+    def __init__(self, width: int, height: int, budget_bytes: int = 0):
+        lib = _lib.load()
+        h = C.c_void_p()
+        check(lib.mmr_create_ex(width, height, budget_bytes, C.byref(h)), None)
+        self._lib = lib
+        self._h = h
+        self.W, self.H = width, height
+        self.n = 0
+        self.dtype = None
+        self._points = None
+
+    # -- lifetime
+    def close(self):
+        if self._h:
+            self._lib.mmr_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status):
+        check(status, self._h)
+
+    # -- data
+    def alloc_points(self, n: int, dtype: str = "f32") -> torch.Tensor:
+        p = C.c_void_p()
+        self._check(self._lib.mmr_alloc_points(self._h, n, DTYPE_CODE[dtype], C.byref(p)))
+        self.n, self.dtype = n, dtype
+        tdt, typestr = _TORCH_VIEW[dtype]
+        self._points = device_view(p.value, (n, 3), typestr)
+        return self._points
+
+    @property
+    def points(self) -> torch.Tensor:
+        return self._points
+
+    def alloc_colors(self) -> torch.Tensor:
+        p = C.c_void_p()
+        self._check(self._lib.mmr_alloc_colors(self._h, C.byref(p)))
+        return device_view(p.value, (self.n,), "<i4")
+
+    # -- parameters
+    def set_camera(self, eye, target, up, fovy_deg, znear, zfar):
+        d3 = C.c_double * 3
+        self._check(self._lib.mmr_set_camera(self._h, d3(*eye), d3(*target), d3(*up), fovy_deg, znear, zfar))
+
+    def set_matrix(self, m, znear, zfar):
+        vals = [float(v) for v in torch.as_tensor(m, dtype=torch.float32).reshape(-1).tolist()]
+        self._check(self._lib.mmr_set_matrix(self._h, (C.c_float * 16)(*vals), znear, zfar))
+
+    def get_matrix(self):
+        out = (C.c_float * 16)()
+        self._check(self._lib.mmr_get_matrix(self._h, out))
+        return list(out)
+
+    def set_sim(self, seed: int, cloud: int = 0, amplitude: float = 1e-3, first_step: int = 0):
+        self._check(self._lib.mmr_set_sim(self._h, seed, cloud, amplitude, first_step))
+
+    def set_style(self, color: int = 0xFFFFFFFF, background: int = 0):
+        self._check(self._lib.mmr_set_style(self._h, color, background))
+
+    def set_launch(self, threads: int = 256, ctas_per_sm: int = 0):
+        self._check(self._lib.mmr_set_launch(self._h, threads, ctas_per_sm))
+
+    # -- frames
+    def step_and_render(self, stream=None):
+        self._check(self._lib.mmr_step_and_render(self._h, stream_handle(stream)))
+
+    def displace(self, stream=None):
+        self._check(self._lib.mmr_displace(self._h, stream_handle(stream)))
+
+    def render(self, stream=None):
+        self._check(self._lib.mmr_render(self._h, stream_handle(stream)))
+
+    def step_and_render_roundtrip(self, stream=None, pinned: bool = True):
+        self._check(self._lib.mmr_step_and_render_roundtrip(self._h, stream_handle(stream), int(pinned)))
+
+    def frame_ptrs(self):
+        r, k = C.c_void_p(), C.c_void_p()
+        self._check(self._lib.mmr_frame_ptr(self._h, C.byref(r), C.byref(k)))
+        return r.value, k.value
+
+    def frame_rgba(self) -> torch.Tensor:
+        """int32[H, W] view of the RGBA8 framebuffer (reinterpret as uint32)."""
+        r, _ = self.frame_ptrs()
+        return device_view(r, (self.H, self.W), "<i4")
+
+    def frame_keys(self) -> torch.Tensor:
+        """int64[H, W] view of the latest depth-id keys (reinterpret as uint64)."""
+        _, k = self.frame_ptrs()
+        return device_view(k, (self.H, self.W), "<i8")
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._lib.mmr_set_timing(self._h, int(enable)))
+
+    def last_kernel_ms(self):
+        """(point kernel ms, resolve kernel ms) of the latest timed frame."""
+        a, b = C.c_float(), C.c_float()
+        self._check(self._lib.mmr_last_kernel_ms(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    @property
+    def step(self) -> int:
+        s = C.c_uint32()
+        self._check(self._lib.mmr_get_step(self._h, C.byref(s)))
+        return s.value
+
+    @property
+    def device_bytes(self) -> int:
+        b = C.c_uint64()
+        self._check(self._lib.mmr_device_bytes(self._h, C.byref(b)))
+        return b.value
+
+
+__all__ = ["Context", "MmrError", "device_view"]

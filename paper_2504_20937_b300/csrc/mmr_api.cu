@@ -1,0 +1,614 @@
+// libmmr C ABI: context, point allocation, camera, frames (see include/mmr.h).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mmr.h"
+#include "mmr_device.cuh"
+#include "mmr_internal.h"
+
+namespace {
+
+thread_local char g_create_error[512] = "";
+
+}  // namespace
+
+struct mmr_ctx {
+    int device = 0;
+    int W = 0, H = 0;
+    uint64_t budget = 0;          // 0 = unlimited
+    uint64_t held = 0;            // device bytes held
+    mmr::LaunchShape launch;
+
+    unsigned long long *keys[2] = {nullptr, nullptr};
+    int splat_buf = 0;            // key buffer the next frame splats into
+    int latest_buf = 0;           // key buffer holding the latest frame
+    uint32_t *rgba = nullptr;
+
+    void *points = nullptr;
+    uint64_t n = 0;
+    int dtype = 0;
+    uint64_t point_bytes = 0;
+    uint32_t *colors = nullptr;
+
+    // round-trip baseline buffers (allocated on first use)
+    void *rt_device = nullptr;
+    void *rt_host = nullptr;
+    int rt_host_pinned = -1;
+
+    mmr::Cam cam{};
+    bool have_cam = false;
+    float matrix[16] = {};
+
+    uint64_t seed = 0;
+    uint32_t cloud = 0;
+    float amplitude = 0.0f;
+    uint32_t step = 0;
+    uint32_t color = 0xFFFFFFFFu;
+    uint32_t background = 0u;
+
+    bool timing = false;
+    bool timed_frame = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+
+    char err[512] = "";
+};
+
+namespace {
+
+mmr_status fail(mmr_ctx *c, mmr_status s, const char *fmt, ...)
+{
+    char *dst = c ? c->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mmr_status cuda_fail(mmr_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, MMR_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Test hook: MMR_FAIL_ALLOC_AFTER=k makes every device allocation after the
+// first k in this process report out-of-memory (host-side, no device fault).
+bool injected_alloc_failure()
+{
+    static long long count = 0;
+    const char *v = getenv("MMR_FAIL_ALLOC_AFTER");
+    if (!v || !*v)
+        return false;
+    return count++ >= atoll(v);
+}
+
+mmr_status dev_alloc(mmr_ctx *c, void **p, uint64_t bytes, const char *what)
+{
+    *p = nullptr;
+    if (c->budget && c->held + bytes > c->budget)
+        return fail(c, MMR_ERR_BUDGET, "%s: %llu bytes would exceed the budget (%llu of %llu held)",
+                    what, (unsigned long long)bytes, (unsigned long long)c->held,
+                    (unsigned long long)c->budget);
+    if (injected_alloc_failure())
+        return fail(c, MMR_ERR_OOM, "%s: injected allocation failure", what);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? MMR_ERR_OOM : MMR_ERR_CUDA,
+                    "%s: cudaMalloc(%llu) failed: %s", what, (unsigned long long)bytes,
+                    cudaGetErrorString(e));
+    }
+    c->held += bytes;
+    return MMR_OK;
+}
+
+void dev_free(mmr_ctx *c, void **p, uint64_t bytes)
+{
+    if (*p) {
+        cudaFree(*p);
+        c->held -= bytes;
+        *p = nullptr;
+    }
+}
+
+uint64_t frame_px(const mmr_ctx *c) { return (uint64_t)c->W * (uint64_t)c->H; }
+
+uint64_t bytes_per_point(int dtype) { return dtype == MMR_F32x3 ? 12u : 6u; }
+
+// Storage is padded to whole 48-byte groups so the vector path never reads
+// past the allocation.
+uint64_t storage_bytes(uint64_t n, int dtype)
+{
+    const uint64_t raw = n * bytes_per_point(dtype);
+    return (raw + 47) / 48 * 48;
+}
+
+mmr::PointParams point_params(const mmr_ctx *c)
+{
+    mmr::PointParams P{};
+    P.cam = c->cam;
+    P.keys = c->keys[c->splat_buf];
+    P.W = c->W;
+    P.H = c->H;
+    P.fW = (float)c->W;
+    P.fH = (float)c->H;
+    P.halfW = 0.5f * (float)c->W;
+    P.halfH = 0.5f * (float)c->H;
+    P.seed_lo = (uint32_t)(c->seed & 0xffffffffu);
+    P.seed_hi = (uint32_t)(c->seed >> 32);
+    P.step = c->step;
+    P.cloud = c->cloud;
+    P.amplitude = c->amplitude;
+    P.id_base = 0;
+    return P;
+}
+
+mmr_status check_frame_ready(mmr_ctx *c, bool need_cam)
+{
+    if (!c->points)
+        return fail(c, MMR_ERR_STATE, "no points allocated (call mmr_alloc_points first)");
+    if (need_cam && !c->have_cam)
+        return fail(c, MMR_ERR_STATE, "no camera set (call mmr_set_camera or mmr_set_matrix first)");
+    return MMR_OK;
+}
+
+// Render the current point buffer `pos` into the splat key buffer, then
+// resolve and flip buffers.  `displace` fuses the step into the same kernel.
+mmr_status frame(mmr_ctx *c, void *pos, bool displace, cudaStream_t s)
+{
+    mmr::PointParams P = point_params(c);
+    if (c->timing)
+        cudaEventRecord(c->ev[0], s);
+    cudaError_t e = mmr::launch_points(c->dtype, pos, (uint32_t)c->n, P, displace, true, c->launch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "point kernel launch");
+    if (c->timing)
+        cudaEventRecord(c->ev[1], s);
+    const int cur = c->splat_buf;
+    e = mmr::launch_resolve(c->keys[cur], c->keys[cur ^ 1], c->rgba, c->colors, (uint32_t)frame_px(c),
+                            c->color, c->background, c->launch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "resolve kernel launch");
+    if (c->timing) {
+        cudaEventRecord(c->ev[2], s);
+        c->timed_frame = true;
+    }
+    c->latest_buf = cur;
+    c->splat_buf = cur ^ 1;
+    if (displace)
+        c->step += 1;
+    return MMR_OK;
+}
+
+}  // namespace
+
+namespace mmr {
+
+bool build_clip_matrix(const double eye[3], const double target[3], const double up[3],
+                       double fovy_deg, double aspect, double znear, double zfar, float out[16])
+{
+    // View: forward f = normalize(target - eye), side s = normalize(f x up),
+    // true up u = s x f.  Perspective: g = cot(fovy/2).  M = P * V in FP64.
+    double f[3] = {target[0] - eye[0], target[1] - eye[1], target[2] - eye[2]};
+    const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0) || !std::isfinite(fl))
+        return false;
+    for (double &v : f)
+        v /= fl;
+    double s[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    const double sl = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    if (!(sl > 0.0) || !std::isfinite(sl))
+        return false;   // up parallel to the view direction
+    for (double &v : s)
+        v /= sl;
+    const double u[3] = {s[1] * f[2] - s[2] * f[1], s[2] * f[0] - s[0] * f[2], s[0] * f[1] - s[1] * f[0]};
+    auto dot = [](const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+    const double view[4][4] = {
+        {s[0], s[1], s[2], -dot(s, eye)},
+        {u[0], u[1], u[2], -dot(u, eye)},
+        {-f[0], -f[1], -f[2], dot(f, eye)},
+        {0.0, 0.0, 0.0, 1.0},
+    };
+    const double kPi = 3.14159265358979323846;
+    const double g = 1.0 / std::tan(0.5 * fovy_deg * (kPi / 180.0));
+    const double proj[4][4] = {
+        {g / aspect, 0.0, 0.0, 0.0},
+        {0.0, g, 0.0, 0.0},
+        {0.0, 0.0, (zfar + znear) / (znear - zfar), 2.0 * zfar * znear / (znear - zfar)},
+        {0.0, 0.0, -1.0, 0.0},
+    };
+    for (int r = 0; r < 4; ++r)
+        for (int col = 0; col < 4; ++col) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; ++k)
+                acc += proj[r][k] * view[k][col];
+            out[4 * r + col] = (float)acc;
+        }
+    return true;
+}
+
+}  // namespace mmr
+
+// ============================================================== C ABI
+
+extern "C" {
+
+const char *mmr_status_string(mmr_status s)
+{
+    switch (s) {
+    case MMR_OK: return "ok";
+    case MMR_ERR_INVALID_ARG: return "invalid argument";
+    case MMR_ERR_OOM: return "out of memory";
+    case MMR_ERR_BUDGET: return "over device-memory budget";
+    case MMR_ERR_CUDA: return "CUDA error";
+    case MMR_ERR_STATE: return "call out of order";
+    case MMR_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+const char *mmr_last_error(const mmr_ctx *ctx) { return ctx ? ctx->err : g_create_error; }
+
+mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx **out)
+{
+    if (!out)
+        return fail(nullptr, MMR_ERR_INVALID_ARG, "mmr_create: out is NULL");
+    *out = nullptr;
+    if (width < 1 || height < 1 || width > 32768 || height > 32768)
+        return fail(nullptr, MMR_ERR_INVALID_ARG, "mmr_create: size %dx%d outside 1..32768", width, height);
+    mmr_ctx *c = new (std::nothrow) mmr_ctx();
+    if (!c)
+        return fail(nullptr, MMR_ERR_OOM, "mmr_create: host allocation failed");
+    c->W = width;
+    c->H = height;
+    c->budget = budget_bytes;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->launch.sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(nullptr, MMR_ERR_CUDA, "mmr_create: no usable CUDA device: %s", cudaGetErrorString(e));
+        delete c;
+        return MMR_ERR_CUDA;
+    }
+    const uint64_t npx = frame_px(c);
+    mmr_status st = dev_alloc(c, (void **)&c->keys[0], npx * 8, "depth-id buffer 0");
+    if (st == MMR_OK)
+        st = dev_alloc(c, (void **)&c->keys[1], npx * 8, "depth-id buffer 1");
+    if (st == MMR_OK)
+        st = dev_alloc(c, (void **)&c->rgba, npx * 4, "RGBA framebuffer");
+    if (st == MMR_OK) {
+        e = cudaMemset(c->keys[0], 0xff, npx * 8);
+        if (e == cudaSuccess)
+            e = cudaMemset(c->keys[1], 0xff, npx * 8);
+        if (e == cudaSuccess)
+            e = cudaMemset(c->rgba, 0, npx * 4);
+        if (e == cudaSuccess)
+            e = cudaDeviceSynchronize();
+        if (e != cudaSuccess)
+            st = cuda_fail(c, e, "mmr_create: clearing buffers");
+    }
+    if (st != MMR_OK) {
+        snprintf(g_create_error, sizeof g_create_error, "%s", c->err);
+        mmr_destroy(c);
+        return st;
+    }
+    g_create_error[0] = 0;
+    *out = c;
+    return MMR_OK;
+}
+
+mmr_status mmr_create(int width, int height, mmr_ctx **out) { return mmr_create_ex(width, height, 0, out); }
+
+mmr_status mmr_destroy(mmr_ctx *ctx)
+{
+    if (!ctx)
+        return MMR_OK;
+    cudaDeviceSynchronize();
+    dev_free(ctx, (void **)&ctx->keys[0], frame_px(ctx) * 8);
+    dev_free(ctx, (void **)&ctx->keys[1], frame_px(ctx) * 8);
+    dev_free(ctx, (void **)&ctx->rgba, frame_px(ctx) * 4);
+    dev_free(ctx, &ctx->points, storage_bytes(ctx->n, ctx->dtype));
+    dev_free(ctx, (void **)&ctx->colors, ctx->n * 4);
+    dev_free(ctx, &ctx->rt_device, storage_bytes(ctx->n, ctx->dtype));
+    if (ctx->rt_host) {
+        if (ctx->rt_host_pinned == 1)
+            cudaFreeHost(ctx->rt_host);
+        else
+            free(ctx->rt_host);
+    }
+    for (cudaEvent_t &ev : ctx->ev)
+        if (ev)
+            cudaEventDestroy(ev);
+    delete ctx;
+    return MMR_OK;
+}
+
+mmr_status mmr_alloc_points(mmr_ctx *ctx, uint64_t n, int dtype, void **dev_ptr)
+{
+    if (!ctx || !dev_ptr)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_points: NULL argument");
+    *dev_ptr = nullptr;
+    if (n == 0 || n >= (1ull << 32))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_points: n=%llu outside 1..2^32-1",
+                    (unsigned long long)n);
+    if (dtype != MMR_F32x3 && dtype != MMR_F16x3 && dtype != MMR_BF16x3)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_points: unknown dtype %d", dtype);
+    if (ctx->points)
+        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_points: this context already has points");
+    const uint64_t bytes = storage_bytes(n, dtype);
+    mmr_status st = dev_alloc(ctx, &ctx->points, bytes, "point buffer");
+    if (st != MMR_OK)
+        return st;
+    cudaError_t e = cudaMemset(ctx->points, 0, bytes);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dev_free(ctx, &ctx->points, bytes);
+        return cuda_fail(ctx, e, "mmr_alloc_points: clearing");
+    }
+    ctx->n = n;
+    ctx->dtype = dtype;
+    ctx->point_bytes = n * bytes_per_point(dtype);
+    *dev_ptr = ctx->points;
+    return MMR_OK;
+}
+
+mmr_status mmr_alloc_colors(mmr_ctx *ctx, uint32_t **dev_colors)
+{
+    if (!ctx || !dev_colors)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_colors: NULL argument");
+    *dev_colors = nullptr;
+    if (!ctx->points)
+        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_colors: allocate points first");
+    if (!ctx->colors) {
+        mmr_status st = dev_alloc(ctx, (void **)&ctx->colors, ctx->n * 4, "colour buffer");
+        if (st != MMR_OK)
+            return st;
+        cudaError_t e = cudaMemset(ctx->colors, 0xff, ctx->n * 4);
+        if (e == cudaSuccess)
+            e = cudaDeviceSynchronize();
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "mmr_alloc_colors: clearing");
+    }
+    *dev_colors = ctx->colors;
+    return MMR_OK;
+}
+
+mmr_status mmr_set_matrix(mmr_ctx *ctx, const float m[16], float znear, float zfar)
+{
+    if (!ctx || !m)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: NULL argument");
+    if (!(znear > 0.0f) || !(zfar > znear) || !std::isfinite(zfar))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: need 0 < znear < zfar < inf");
+    for (int k = 0; k < 16; ++k)
+        if (!std::isfinite(m[k]))
+            return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: non-finite entry %d", k);
+    memcpy(ctx->matrix, m, sizeof ctx->matrix);
+    for (int k = 0; k < 4; ++k) {
+        ctx->cam.rx[k] = m[k];
+        ctx->cam.ry[k] = m[4 + k];
+        ctx->cam.rw[k] = m[12 + k];
+    }
+    ctx->cam.znear = znear;
+    ctx->cam.zfar = zfar;
+    ctx->have_cam = true;
+    return MMR_OK;
+}
+
+mmr_status mmr_get_matrix(const mmr_ctx *ctx, float m[16])
+{
+    if (!ctx || !m)
+        return MMR_ERR_INVALID_ARG;
+    if (!ctx->have_cam)
+        return MMR_ERR_STATE;
+    memcpy(m, ctx->matrix, sizeof ctx->matrix);
+    return MMR_OK;
+}
+
+mmr_status mmr_set_camera(mmr_ctx *ctx, const double eye[3], const double target[3],
+                          const double up[3], double fovy_deg, double znear, double zfar)
+{
+    if (!ctx || !eye || !target || !up)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: NULL argument");
+    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: need 0 < fovy < 180, 0 < znear < zfar");
+    float m[16];
+    if (!mmr::build_clip_matrix(eye, target, up, fovy_deg, (double)ctx->W / (double)ctx->H, znear, zfar, m))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: eye == target or up parallel to view");
+    return mmr_set_matrix(ctx, m, (float)znear, (float)zfar);
+}
+
+mmr_status mmr_set_sim(mmr_ctx *ctx, uint64_t seed, uint32_t cloud, float amplitude, uint32_t first_step)
+{
+    if (!ctx)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_sim: NULL ctx");
+    if (!(amplitude >= 0.0f && amplitude <= 1.0f))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_sim: amplitude must be in [0, 1]");
+    ctx->seed = seed;
+    ctx->cloud = cloud;
+    ctx->amplitude = amplitude;
+    ctx->step = first_step;
+    return MMR_OK;
+}
+
+mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    ctx->color = color;
+    ctx->background = background;
+    return MMR_OK;
+}
+
+mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (threads < 32 || threads > 1024 || threads % 32 != 0 || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: threads %d / ctas_per_sm %d out of range",
+                    threads, ctas_per_sm);
+    ctx->launch.threads = threads;
+    ctx->launch.ctas_per_sm = ctas_per_sm;
+    return MMR_OK;
+}
+
+mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = check_frame_ready(ctx, true);
+    if (st != MMR_OK)
+        return st;
+    return frame(ctx, ctx->points, true, (cudaStream_t)stream);
+}
+
+mmr_status mmr_render(mmr_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = check_frame_ready(ctx, true);
+    if (st != MMR_OK)
+        return st;
+    return frame(ctx, ctx->points, false, (cudaStream_t)stream);
+}
+
+mmr_status mmr_displace(mmr_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = check_frame_ready(ctx, false);
+    if (st != MMR_OK)
+        return st;
+    mmr::PointParams P = point_params(ctx);
+    cudaError_t e = mmr::launch_points(ctx->dtype, ctx->points, (uint32_t)ctx->n, P, true, false,
+                                       ctx->launch, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "displace kernel launch");
+    ctx->step += 1;
+    return MMR_OK;
+}
+
+mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int pinned_host)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = check_frame_ready(ctx, true);
+    if (st != MMR_OK)
+        return st;
+    const int want_pinned = pinned_host ? 1 : 0;
+    const uint64_t bytes = storage_bytes(ctx->n, ctx->dtype);
+    if (ctx->rt_host && ctx->rt_host_pinned != want_pinned) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e, "round-trip: sync before switching host buffer");
+        if (ctx->rt_host_pinned == 1)
+            cudaFreeHost(ctx->rt_host);
+        else
+            free(ctx->rt_host);
+        ctx->rt_host = nullptr;
+    }
+    if (!ctx->rt_host) {
+        if (want_pinned) {
+            cudaError_t e = cudaMallocHost(&ctx->rt_host, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ctx->rt_host = nullptr;
+                return fail(ctx, MMR_ERR_OOM, "round-trip: pinned host allocation failed: %s",
+                            cudaGetErrorString(e));
+            }
+        } else {
+            ctx->rt_host = malloc(bytes);
+            if (!ctx->rt_host)
+                return fail(ctx, MMR_ERR_OOM, "round-trip: host allocation failed");
+        }
+        ctx->rt_host_pinned = want_pinned;
+    }
+    if (!ctx->rt_device) {
+        st = dev_alloc(ctx, &ctx->rt_device, bytes, "round-trip device copy");
+        if (st != MMR_OK)
+            return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st = mmr_displace(ctx, stream);
+    if (st != MMR_OK)
+        return st;
+    cudaError_t e = cudaMemcpyAsync(ctx->rt_host, ctx->points, ctx->point_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->rt_device, ctx->rt_host, ctx->point_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "round-trip copies");
+    return frame(ctx, ctx->rt_device, false, s);
+}
+
+mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **depth_id)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (rgba)
+        *rgba = ctx->rgba;
+    if (depth_id)
+        *depth_id = reinterpret_cast<const uint64_t *>(ctx->keys[ctx->latest_buf]);
+    return MMR_OK;
+}
+
+mmr_status mmr_get_step(const mmr_ctx *ctx, uint32_t *step)
+{
+    if (!ctx || !step)
+        return MMR_ERR_INVALID_ARG;
+    *step = ctx->step;
+    return MMR_OK;
+}
+
+mmr_status mmr_set_timing(mmr_ctx *ctx, int enable)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (enable && !ctx->ev[0]) {
+        for (cudaEvent_t &ev : ctx->ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e, "mmr_set_timing: cudaEventCreate");
+        }
+    }
+    ctx->timing = enable != 0;
+    ctx->timed_frame = false;
+    return MMR_OK;
+}
+
+mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *resolve_ms)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (!ctx->timing || !ctx->timed_frame)
+        return fail(ctx, MMR_ERR_STATE, "mmr_last_kernel_ms: timing off or no timed frame yet");
+    cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
+    float a = 0.0f, b = 0.0f;
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]);
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_last_kernel_ms");
+    if (point_ms)
+        *point_ms = a;
+    if (resolve_ms)
+        *resolve_ms = b;
+    return MMR_OK;
+}
+
+mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes)
+{
+    if (!ctx || !bytes)
+        return MMR_ERR_INVALID_ARG;
+    *bytes = ctx->held;
+    return MMR_OK;
+}
+
+}  // extern "C"

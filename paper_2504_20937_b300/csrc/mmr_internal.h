@@ -1,0 +1,28 @@
+// Host-side declarations shared by the libmmr translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mmr {
+
+struct PointParams;
+
+struct LaunchShape {
+    int threads = 256;       // threads per block
+    int ctas_per_sm = 0;     // 0: one thread per work item; else a persistent grid
+    int sm_count = 148;
+};
+
+cudaError_t launch_points(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
+                          bool splat, const LaunchShape &ls, cudaStream_t s);
+
+cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys,
+                           uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,
+                           uint32_t background, const LaunchShape &ls, cudaStream_t s);
+
+// FP64 camera -> FP32 clip matrix (row-major 4x4); returns false on invalid input.
+bool build_clip_matrix(const double eye[3], const double target[3], const double up[3],
+                       double fovy_deg, double aspect, double znear, double zfar, float out[16]);
+
+}  // namespace mmr

@@ -1,0 +1,122 @@
+"""Parity at the benchmark sizes, in the launch configuration the bench
+times (the library defaults).
+
+4M-point 1920x1080 orbit: the first frames are compared whole against the
+oracle; after 1000 frames, sampled points are followed one by one by the
+oracle and the frame is checked through its winners.  64M-point 16-cluster
+Gaussian mixture at 3840x2160: one whole frame in FP32, binary16 and
+bfloat16 storage against the oracle, plus the binary16 accuracy gates
+against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2504_20937_b300 import inputs
+
+from ._harness import CENTRE, UP, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2_start():
+    sc = inputs.C2
+    return sc, inputs.encode(sc.positions(), "f32")
+
+
+def test_c2_first_frames_bit_exact(c2_start):
+    sc, stored = c2_start
+    args = (stored, "f32", sc.W, sc.H, sc.philox_seed, sc.amplitude, 3, sc.eye)
+    g = gpu_run(*args)
+    o = oracle_run(*args)
+    assert np.array_equal(g[0], o[0])
+    assert np.array_equal(g[1], o[1])
+    assert np.array_equal(g[2], o[2])
+
+
+def test_c2_1000_frames_sampled(c2_start):
+    sc, stored = c2_start
+    frames = sc.frames
+    gpos, gkeys, grgba, _ = gpu_run(stored, "f32", sc.W, sc.H, sc.philox_seed, sc.amplitude, frames, sc.eye)
+    # invariants of the whole state
+    assert gpos.shape == stored.shape and np.all(np.isfinite(gpos))
+    assert gpos.min() >= 0.0 and gpos.max() <= 1.0
+    covered = gkeys != oracle.EMPTY_KEY
+    assert np.array_equal(grgba[covered], np.full(covered.sum(), sc.color, np.uint32))
+    assert np.all(grgba[~covered] == sc.background)
+    ids = (gkeys[covered] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    assert ids.max() < sc.n
+    # sampled points followed one by one through all frames by the oracle
+    rng = np.random.default_rng(7)
+    sample = np.unique(np.concatenate([rng.choice(sc.n, 3000, replace=False),
+                                       rng.choice(ids, 3000, replace=False), [0, sc.n - 1]]))
+    sample = sample.astype(np.uint32)
+    pos = stored[sample].copy()
+    for f in range(frames):
+        oracle.displace_ids_f32(pos, sample, sc.philox_seed, 0, f, np.float32(sc.amplitude))
+    np.testing.assert_array_equal(gpos[sample], pos)
+    # every sampled point: its key at its pixel is >= the stored minimum, and
+    # equal exactly when it is that pixel's winner
+    M = oracle.camera_f32(sc.eye(frames - 1), CENTRE, UP, sc.fovy_deg, sc.aspect, sc.znear, sc.zfar)
+    px, w = oracle.project_f32(M, pos, sc.W, sc.H, np.float32(sc.znear), np.float32(sc.zfar))
+    on = px != 0xFFFFFFFF
+    key = (w.view(np.uint32).astype(np.uint64) << np.uint64(32)) | sample.astype(np.uint64)
+    assert np.all(gkeys[px[on]] <= key[on])
+    winner = (gkeys[px[on]] & np.uint64(0xFFFFFFFF)) == sample[on]
+    assert np.array_equal(gkeys[px[on]][winner], key[on][winner])
+    assert winner.sum() > 1000                 # the sampled winners were checked
+
+
+@pytest.fixture(scope="module")
+def c3_start():
+    sc = inputs.C3
+    return sc, sc.positions()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_c3_frame_bit_exact(c3_start, dtype):
+    sc, pos64 = c3_start
+    stored = inputs.encode(pos64, dtype)
+    args = (stored, dtype, sc.W, sc.H, sc.philox_seed, sc.amplitude, 1, sc.eye)
+    g = gpu_run(*args)
+    o = oracle_run(*args)
+    assert np.array_equal(g[0], o[0])
+    bad = np.count_nonzero(g[1] != o[1])
+    assert bad == 0, f"{bad} pixels differ"
+    assert np.array_equal(g[2], o[2])
+
+
+def _agreement(keys_a, keys_b):
+    """Share of pixels where both are empty, or both covered with depths
+    within 2^-9 relative (ids may differ between near-equal depths)."""
+    ea, eb = keys_a == oracle.EMPTY_KEY, keys_b == oracle.EMPTY_KEY
+    da = (keys_a >> np.uint64(32)).astype(np.uint32).view(np.float32).astype(np.float64)
+    db = (keys_b >> np.uint64(32)).astype(np.uint32).view(np.float32).astype(np.float64)
+    both = ~ea & ~eb
+    close = np.zeros_like(ea)
+    close[both] = np.abs(da[both] - db[both]) <= 2.0**-9 * np.abs(db[both])
+    return float(np.mean((ea & eb) | close))
+
+
+def test_c3_f16_accuracy_gates(c3_start):
+    """binary16 storage: after one step every coordinate is within 2^-10
+    relative (floor 2^-14) of the FP64 oracle stepped from the same stored
+    input, and >= 99.9% of pixels agree with the frame of the FP64 positions.
+    bfloat16 is measured the same way and only reported."""
+    sc, pos64 = c3_start
+    report = {}
+    for dtype in ("f16", "bf16"):
+        stored = inputs.encode(pos64, dtype)
+        g = gpu_run(stored, dtype, sc.W, sc.H, sc.philox_seed, sc.amplitude, 1, sc.eye)
+        p64 = oracle.from_storage(stored, dtype).astype(np.float64)
+        oracle.displace_f64(p64, sc.philox_seed, 0, 0, float(np.float32(sc.amplitude)))
+        got = oracle.from_storage(g[0], dtype).astype(np.float64)
+        rel = np.abs(got - p64) / np.maximum(np.abs(p64), 2.0**-14)
+        M = oracle.camera_f32(sc.eye(0), CENTRE, UP, sc.fovy_deg, sc.aspect, sc.znear, sc.zfar)
+        k64, _ = oracle.render(p64.astype(np.float32), "f32", M, sc.W, sc.H, np.float32(sc.znear),
+                               np.float32(sc.zfar))
+        report[dtype] = (float(rel.max()), _agreement(g[1], k64))
+    print("16-bit storage vs FP64 oracle (max rel err, pixel agreement):", report)
+    assert report["f16"][0] <= 2.0**-10
+    assert report["f16"][1] >= 0.999

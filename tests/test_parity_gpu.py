@@ -1,0 +1,131 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP32 storage: positions, depth-id keys and RGBA must be bit-identical.
+16-bit storage: bit-identical to the oracle replaying the same storage
+rounding.  Sizes span several thread groups and blocks with ragged tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_20937_b300 import inputs
+
+from ._harness import fixed_eye, gpu_run, oracle_run, orbit
+
+pytestmark = pytest.mark.gpu
+
+
+def _assert_same(gpu, orc, what=""):
+    gpos, gkeys, grgba, _ = gpu
+    opos, okeys, orgba, _ = orc
+    assert gpos.dtype == opos.dtype
+    np.testing.assert_array_equal(gpos.view(np.uint8), opos.view(np.uint8), err_msg=f"positions {what}")
+    bad = np.nonzero(gkeys != okeys)[0]
+    assert bad.size == 0, f"keys {what}: {bad.size} pixels differ, first {bad[:5]}"
+    np.testing.assert_array_equal(grgba, orgba, err_msg=f"rgba {what}")
+
+
+def test_pr1_reference_config_bit_exact():
+    """65,536 uniform points (seed 0), 100 steps of a = 1e-3, 512 x 512,
+    fixed camera at (0.5, 0.5, 2.5): final positions and frame bit-exact,
+    plus frames 0, 1 and 50 along the way."""
+    sc = inputs.PR1
+    stored = inputs.encode(sc.positions(), "f32")
+    keep = {0, 1, 50}
+    g = gpu_run(stored, "f32", sc.W, sc.H, sc.philox_seed, sc.amplitude, sc.frames, fixed_eye, keep_every=keep)
+    o = oracle_run(stored, "f32", sc.W, sc.H, sc.philox_seed, sc.amplitude, sc.frames, fixed_eye,
+                   keep_every=keep)
+    _assert_same(g, o, "PR1 final")
+    for f in keep:
+        assert np.array_equal(g[3][f][0], o[3][f][0]), f"keys frame {f}"
+        assert np.array_equal(g[3][f][1], o[3][f][1]), f"rgba frame {f}"
+    covered = (g[1] != oracle.EMPTY_KEY).sum()
+    assert covered > 10_000                  # the cloud is actually visible
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 9, 255, 1000, 4097, 65537])
+def test_ragged_sizes_bit_exact(dtype, n):
+    W, H = 37, 23                             # W*H = 851: not a multiple of 4
+    stored = inputs.encode(inputs.uniform_cloud(n, 100 + n), dtype)
+    args = (stored, dtype, W, H, 7, 2e-3, 3, orbit(5.0))
+    _assert_same(gpu_run(*args), oracle_run(*args), f"{dtype} n={n}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_gaussian_cluster_contention_bit_exact(dtype):
+    """Many points per pixel: 200k points in a 3-cluster mixture at 96 x 64."""
+    n = 200_000
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 21, components=3, sigma=0.02), dtype)
+    args = (stored, dtype, 96, 64, 9, 5e-4, 2, fixed_eye)
+    _assert_same(gpu_run(*args), oracle_run(*args), dtype)
+
+
+@pytest.mark.parametrize("launch", [(32, 0), (128, 0), (1024, 0), (256, 1), (64, 3), (512, 8)])
+def test_launch_shape_does_not_change_results(launch):
+    n = 70_001
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 22, components=4, sigma=0.05), "f32")
+    args = (stored, "f32", 160, 90, 3, 1e-3, 3, orbit(10.0))
+    _assert_same(gpu_run(*args, launch=launch), oracle_run(*args), f"launch {launch}")
+
+
+@pytest.mark.parametrize("mode", ["split", "roundtrip", "roundtrip_pageable"])
+def test_split_and_roundtrip_paths_match(mode):
+    n = 50_003
+    stored = inputs.encode(inputs.uniform_cloud(n, 23), "f32")
+    args = (stored, "f32", 200, 120, 4, 1e-3, 4, orbit(3.0))
+    _assert_same(gpu_run(*args, mode=mode), oracle_run(*args), mode)
+
+
+def test_colour_buffer_and_style():
+    n = 30_000
+    stored = inputs.encode(inputs.uniform_cloud(n, 24), "f32")
+    colors = np.random.default_rng(0).integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+    args = (stored, "f32", 128, 128, 5, 1e-3, 2, fixed_eye)
+    kw = dict(colors=colors, background=0x12345678)
+    g = gpu_run(*args, **kw)
+    _assert_same(g, oracle_run(*args, **kw), "colours")
+    kw = dict(color=0xFF00FF00, background=0x0000FF00)
+    _assert_same(gpu_run(*args, **kw), oracle_run(*args, **kw), "style")
+
+
+def test_camera_matrix_matches_oracle():
+    from paper_2504_20937_b300.api import Context
+    rng = np.random.default_rng(1)
+    with Context(1920, 1080) as ctx:
+        cams = [((0.5, 0.5, 2.5), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)]
+        for f in range(0, 1000, 37):
+            cams.append((inputs.orbit_eye(f, 0.36), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0))
+        for _ in range(30):
+            eye = tuple(rng.uniform(-3, 3, 3))
+            cams.append((eye, tuple(rng.uniform(0, 1, 3)), (0, 1, 0), float(rng.uniform(20, 120)),
+                         0.05, 50.0))
+        for eye, tgt, up, fov, zn, zf in cams:
+            ctx.set_camera(eye, tgt, up, fov, zn, zf)
+            got = np.array(ctx.get_matrix(), np.float32)
+            want = oracle.camera_f32(eye, tgt, up, fov, 1920 / 1080, zn, zf).reshape(-1)
+            assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_empty_and_degenerate_frames():
+    n = 10_000
+    stored = inputs.encode(inputs.uniform_cloud(n, 25), "f32")
+    # depth range beyond the cloud: nothing drawn, all background
+    g = gpu_run(stored, "f32", 64, 48, 1, 1e-3, 1, fixed_eye, znear=50.0, zfar=60.0, background=0xAB)
+    assert np.all(g[1] == oracle.EMPTY_KEY) and np.all(g[2] == 0xAB)
+    # zero amplitude: positions do not move
+    g = gpu_run(stored, "f32", 64, 48, 1, 0.0, 5, fixed_eye)
+    assert np.array_equal(g[0], stored)
+    # all points clamped at a corner: one pixel wins, smallest id at equal depth
+    corner = np.zeros((1000, 3), np.float32)
+    args = (corner, "f32", 33, 17, 2, 1e-3, 1, fixed_eye)
+    g, o = gpu_run(*args), oracle_run(*args)
+    _assert_same(g, o, "corner")
+
+
+def test_single_pixel_framebuffer_and_tall_frame():
+    stored = inputs.encode(inputs.uniform_cloud(5000, 26), "f32")
+    for W, H in [(1, 1), (1, 1000), (999, 1)]:
+        args = (stored, "f32", W, H, 2, 1e-3, 2, fixed_eye)
+        _assert_same(gpu_run(*args), oracle_run(*args), f"{W}x{H}")
