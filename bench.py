@@ -84,9 +84,16 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {
+    "points_kernel_f32_fused": ("mmr_device.cuh", "mmr_kernels.cu", "mmr_points.cuh"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the source files that define `kernel` (ties a committed ncu
+    traffic figure to the code it was measured on)."""
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2504_20937_b300", "csrc"))):
+    for fn in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2504_20937_b300", "csrc", fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -99,7 +106,7 @@ def profiled_traffic(kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():

@@ -173,6 +173,81 @@ MMR_API mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *reso
 /* Device bytes this context holds right now. */
 MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
 
+/* ---- batched clouds --------------------------------------------------------
+ * Many independent clouds, each with its own size, framebuffer, camera and
+ * displacement parameters, advanced and rendered together: one persistent
+ * launch of the point kernel covers every cloud's points and one of the
+ * resolve kernel covers every cloud's pixels.  A device-side frame counter
+ * picks the Philox step, the camera slot and the depth-id buffer, so one
+ * captured frame can be replayed as a CUDA graph with nothing changed on
+ * the host.  Each cloud's result is identical to rendering it alone in its
+ * own mmr_ctx with the same parameters (the per-pixel minimum does not
+ * depend on launch order). */
+typedef struct mmr_batch mmr_batch;
+
+typedef struct mmr_cloud_desc {
+    uint64_t n;            /* points, 1 .. 2^32-1 */
+    int width, height;     /* this cloud's framebuffer, 1..32768 each */
+    uint64_t seed;         /* Philox key (see mmr_set_sim) */
+    uint32_t cloud;        /* Philox counter word 2 */
+    float amplitude;       /* displacement amplitude, [0, 1] */
+    uint32_t color;        /* RGBA8 of every point */
+    uint32_t background;   /* RGBA8 of empty pixels */
+} mmr_cloud_desc;
+
+/* Create a batch of `count` clouds (1..65536) stored as `dtype`, with
+ * `camera_slots` cameras per cloud (frame f uses slot f mod camera_slots,
+ * 1..4096).  All point buffers live in one device allocation (each cloud's
+ * slice 256-byte aligned, zero-filled); every cloud gets two depth-id
+ * buffers and an RGBA8 framebuffer.  budget_bytes as in mmr_create_ex.
+ * The descriptor array is read during the call only. */
+MMR_API mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, int camera_slots,
+                                    uint64_t budget_bytes, mmr_batch **out);
+MMR_API mmr_status mmr_batch_destroy(mmr_batch *b);
+MMR_API const char *mmr_batch_last_error(const mmr_batch *b);
+
+/* Device pointer of cloud `cloud`'s positions (n * 3 coordinates, AoS). */
+MMR_API mmr_status mmr_batch_points(mmr_batch *b, int cloud, void **dev_ptr);
+
+/* Camera of `cloud` in slot `slot`, as mmr_set_camera with the cloud's own
+ * aspect.  Uploaded to the device before the next step or graph replay. */
+MMR_API mmr_status mmr_batch_set_camera(mmr_batch *b, int cloud, int slot, const double eye[3],
+                                        const double target[3], const double up[3], double fovy_deg,
+                                        double znear, double zfar);
+
+/* Launch shape: threads per block (multiple of 32, 32..512), CTAs per SM
+ * of the persistent grid (0 = one CTA per chunk), and point groups per chunk
+ * (1..65536; a group is 48 bytes of positions).  Results never depend on it. */
+MMR_API mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_sm, int chunk_groups);
+
+/* One frame of every cloud: displace + project + splat (one launch), then
+ * resolve + clear (one launch), then advance the device frame counter.
+ * Requires every cloud's camera for the slot the frame uses. */
+MMR_API mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream);
+
+/* `frames` frames by replaying a CUDA graph of one frame (captured on first
+ * use and again after mmr_batch_set_launch).  Same results as calling
+ * mmr_batch_step_and_render `frames` times. */
+MMR_API mmr_status mmr_batch_run_graph(mmr_batch *b, int frames, void *stream);
+
+/* Autotuner: times each candidate launch shape (threads in {128, 256, 512},
+ * CTAs per SM in {0, 1, 2, 4, 8}, chunk groups in {64, 256, 1024}) over
+ * `frames_per_config` frames with CUDA events on `stream`, keeps the fastest
+ * and returns it (any output pointer may be NULL).  Positions and the frame
+ * counter are saved before and restored after, so the simulation state is
+ * unchanged; the frame buffers are cleared.  Allocates a temporary copy of
+ * the positions (counted against the budget). */
+MMR_API mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config, int *threads,
+                                      int *ctas_per_sm, int *chunk_groups, float *best_ms);
+
+/* Latest frame of one cloud (device pointers, as mmr_frame_ptr). */
+MMR_API mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t **rgba,
+                                       const uint64_t **depth_id);
+
+/* Frames enqueued so far, and device bytes held. */
+MMR_API mmr_status mmr_batch_frames(const mmr_batch *b, uint32_t *frames);
+MMR_API mmr_status mmr_batch_device_bytes(const mmr_batch *b, uint64_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,30 @@ SIGNATURES = {
     "mmr_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
 }
 
+
+
+class CloudDesc(C.Structure):
+    """mmr_cloud_desc (include/mmr.h)."""
+    _fields_ = [("n", C.c_uint64), ("width", C.c_int), ("height", C.c_int), ("seed", C.c_uint64),
+                ("cloud", C.c_uint32), ("amplitude", C.c_float), ("color", C.c_uint32),
+                ("background", C.c_uint32)]
+
+
+SIGNATURES.update({
+    "mmr_batch_create": (_i, [_i, C.POINTER(CloudDesc), _i, _i, _u64, C.POINTER(_vp)]),
+    "mmr_batch_destroy": (_i, [_vp]),
+    "mmr_batch_last_error": (C.c_char_p, [_vp]),
+    "mmr_batch_points": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "mmr_batch_set_camera": (_i, [_vp, _i, _i, _d3, _d3, _d3, _d, _d, _d]),
+    "mmr_batch_set_launch": (_i, [_vp, _i, _i, _i]),
+    "mmr_batch_step_and_render": (_i, [_vp, _vp]),
+    "mmr_batch_run_graph": (_i, [_vp, _i, _vp]),
+    "mmr_batch_autotune": (_i, [_vp, _vp, _i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), C.POINTER(_f)]),
+    "mmr_batch_frame_ptr": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp)]),
+    "mmr_batch_frames": (_i, [_vp, C.POINTER(_u32)]),
+    "mmr_batch_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
+})
+
 _lib = None
 
 
@@ -77,9 +101,10 @@ def load() -> C.CDLL:
     return _lib
 
 
-def check(status: int, ctx=None) -> None:
+def check(status: int, ctx=None, batch=False) -> None:
     if status != MMR_OK:
-        msg = load().mmr_last_error(ctx)
+        lib = load()
+        msg = lib.mmr_batch_last_error(ctx) if batch else lib.mmr_last_error(ctx)
         raise MmrError(status, msg.decode() if msg else "")
 
 

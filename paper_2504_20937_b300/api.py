@@ -162,4 +162,96 @@ class Context:
         return b.value
 
 
-__all__ = ["Context", "MmrError", "device_view"]
+class Batch:
+    """Many independent clouds advanced and rendered together (mmr_batch_*).
+
+    clouds: list of dicts with n, width, height, seed, cloud, amplitude and
+    optional color / background.
+    """
+
+    def __init__(self, clouds, dtype: str = "f32", camera_slots: int = 1, budget_bytes: int = 0):
+        lib = _lib.load()
+        arr = (_lib.CloudDesc * len(clouds))()
+        for i, c in enumerate(clouds):
+            arr[i] = _lib.CloudDesc(int(c["n"]), int(c["width"]), int(c["height"]), int(c.get("seed", 0)),
+                                    int(c.get("cloud", i)), float(c.get("amplitude", 1e-3)),
+                                    int(c.get("color", 0xFFFFFFFF)), int(c.get("background", 0)))
+        h = C.c_void_p()
+        check(lib.mmr_batch_create(len(clouds), arr, DTYPE_CODE[dtype], camera_slots, budget_bytes,
+                                   C.byref(h)), None, batch=True)
+        self._lib, self._h = lib, h
+        self.clouds = [dict(c) for c in clouds]
+        self.dtype = dtype
+        self.slots = camera_slots
+
+    def close(self):
+        if self._h:
+            self._lib.mmr_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status):
+        check(status, self._h, batch=True)
+
+    def points(self, i: int) -> torch.Tensor:
+        p = C.c_void_p()
+        self._check(self._lib.mmr_batch_points(self._h, i, C.byref(p)))
+        return device_view(p.value, (int(self.clouds[i]["n"]), 3), _TORCH_VIEW[self.dtype][1])
+
+    def set_camera(self, i: int, slot: int, eye, target, up, fovy_deg, znear, zfar):
+        d3 = C.c_double * 3
+        self._check(self._lib.mmr_batch_set_camera(self._h, i, slot, d3(*eye), d3(*target), d3(*up), fovy_deg,
+                                                   znear, zfar))
+
+    def set_launch(self, threads: int, ctas_per_sm: int, chunk_groups: int):
+        self._check(self._lib.mmr_batch_set_launch(self._h, threads, ctas_per_sm, chunk_groups))
+
+    def step_and_render(self, stream=None):
+        self._check(self._lib.mmr_batch_step_and_render(self._h, stream_handle(stream)))
+
+    def run_graph(self, frames: int, stream=None):
+        self._check(self._lib.mmr_batch_run_graph(self._h, frames, stream_handle(stream)))
+
+    def autotune(self, frames_per_config: int = 3, stream=None):
+        t, c, g, ms = C.c_int(), C.c_int(), C.c_int(), C.c_float()
+        self._check(self._lib.mmr_batch_autotune(self._h, stream_handle(stream), frames_per_config, C.byref(t),
+                                                 C.byref(c), C.byref(g), C.byref(ms)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "chunk_groups": g.value, "ms_per_frame": ms.value}
+
+    def frame_rgba(self, i: int) -> torch.Tensor:
+        r, k = C.c_void_p(), C.c_void_p()
+        self._check(self._lib.mmr_batch_frame_ptr(self._h, i, C.byref(r), C.byref(k)))
+        c = self.clouds[i]
+        return device_view(r.value, (int(c["height"]), int(c["width"])), "<i4")
+
+    def frame_keys(self, i: int) -> torch.Tensor:
+        r, k = C.c_void_p(), C.c_void_p()
+        self._check(self._lib.mmr_batch_frame_ptr(self._h, i, C.byref(r), C.byref(k)))
+        c = self.clouds[i]
+        return device_view(k.value, (int(c["height"]), int(c["width"])), "<i8")
+
+    @property
+    def frames(self) -> int:
+        f = C.c_uint32()
+        self._check(self._lib.mmr_batch_frames(self._h, C.byref(f)))
+        return f.value
+
+    @property
+    def device_bytes(self) -> int:
+        b = C.c_uint64()
+        self._check(self._lib.mmr_batch_device_bytes(self._h, C.byref(b)))
+        return b.value
+
+
+__all__ = ["Batch", "Context", "MmrError", "device_view"]

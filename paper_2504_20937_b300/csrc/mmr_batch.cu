@@ -1,0 +1,717 @@
+// Batched clouds (include/mmr.h, mmr_batch_*): many independent clouds of
+// uneven size, each with its own camera and framebuffer, advanced and
+// rendered by one persistent point launch and one persistent resolve launch
+// per frame.
+//
+// Work is cut into chunks: a point chunk is up to `chunk_groups` 48-byte
+// point groups of one cloud, a pixel chunk up to 4*chunk_groups quads of one
+// cloud's framebuffer.  A persistent CTA strides over the chunk table, so a
+// 1e3-point cloud and a 1e6-point cloud cost in proportion to their size and
+// no CTA idles on a small cloud.  A device-side frame counter selects the
+// Philox step, the camera slot and the depth-id buffer, so a captured frame
+// replays as a CUDA graph with no host update.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mmr.h"
+#include "mmr_device.cuh"
+#include "mmr_internal.h"
+#include "mmr_points.cuh"
+#include "mmr_resolve.cuh"
+
+namespace mmr {
+
+struct CloudDev {
+    void *pos;
+    unsigned long long *keys[2];
+    uint32_t *rgba;
+    uint32_t n;
+    uint32_t npx;
+    int W, H;
+    float fW, fH, halfW, halfH;
+    uint32_t seed_lo, seed_hi, cloud;
+    float amplitude;
+    uint32_t color, background;
+};
+
+struct BatchTables {
+    const CloudDev *clouds;
+    const Cam *cams;            // [slots][count]
+    const uint2 *point_chunks;  // (cloud, first group)
+    const uint2 *pixel_chunks;  // (cloud, first quad)
+    uint32_t n_point_chunks;
+    uint32_t n_pixel_chunks;
+    uint32_t chunk_groups;
+    uint32_t chunk_quads;
+    uint32_t count;
+    uint32_t slots;
+    uint32_t first_step;
+    uint32_t *frame;            // device frame counter
+};
+
+// At most 512 threads per block: the per-chunk cloud parameters held in
+// registers put this kernel above 64 registers per thread.
+constexpr int kBatchMaxThreads = 512;
+
+template <int DT>
+__global__ void __launch_bounds__(kBatchMaxThreads) batch_points_kernel(BatchTables T)
+{
+    const uint32_t frame = *T.frame;
+    const uint32_t slot = frame % T.slots;
+    const int buf = frame & 1;
+    for (uint32_t c = blockIdx.x; c < T.n_point_chunks; c += gridDim.x) {
+        const uint2 ch = T.point_chunks[c];
+        const CloudDev &cl = T.clouds[ch.x];
+        PointParams P;
+        P.cam = T.cams[(size_t)slot * T.count + ch.x];
+        P.keys = cl.keys[buf];
+        P.W = cl.W;
+        P.H = cl.H;
+        P.fW = cl.fW;
+        P.fH = cl.fH;
+        P.halfW = cl.halfW;
+        P.halfH = cl.halfH;
+        P.seed_lo = cl.seed_lo;
+        P.seed_hi = cl.seed_hi;
+        P.step = T.first_step + frame;
+        P.cloud = cl.cloud;
+        P.amplitude = cl.amplitude;
+        P.id_base = 0;
+        const uint32_t n = cl.n;
+        const uint32_t end = min(ch.y + T.chunk_groups, groups_of<DT>(n));
+        for (uint32_t g = ch.y + threadIdx.x; g < end; g += blockDim.x)
+            process_group<DT, true, true>(cl.pos, n, g, P);
+    }
+}
+
+__global__ void batch_resolve_kernel(BatchTables T)
+{
+    const int buf = *T.frame & 1;
+    for (uint32_t c = blockIdx.x; c < T.n_pixel_chunks; c += gridDim.x) {
+        const uint2 ch = T.pixel_chunks[c];
+        const CloudDev &cl = T.clouds[ch.x];
+        const unsigned long long *keys = cl.keys[buf];
+        unsigned long long *next = cl.keys[buf ^ 1];
+        const uint32_t quads = cl.npx / 4;
+        const uint32_t end = min(ch.y + T.chunk_quads, quads);
+        for (uint32_t q = ch.y + threadIdx.x; q < end; q += blockDim.x)
+            resolve_quad(keys, next, cl.rgba, nullptr, q, cl.color, cl.background);
+        if (end == quads && quads * 4 + threadIdx.x < cl.npx)
+            resolve_pixel(keys, next, cl.rgba, nullptr, quads * 4 + threadIdx.x, cl.color, cl.background);
+    }
+}
+
+__global__ void batch_advance_kernel(uint32_t *frame) { *frame += 1u; }
+
+}  // namespace mmr
+
+struct mmr_batch {
+    int device = 0;
+    int count = 0;
+    int dtype = 0;
+    int slots = 1;
+    uint64_t budget = 0;
+    uint64_t held = 0;
+    mmr::LaunchShape launch;
+    uint32_t chunk_groups = 256;
+
+    std::vector<mmr_cloud_desc> desc;
+    std::vector<uint64_t> pos_off;   // byte offset of each cloud's positions
+    std::vector<uint64_t> px_off;    // pixel offset of each cloud's framebuffer
+    uint64_t pos_bytes = 0;
+    uint64_t total_px = 0;
+
+    void *pos_base = nullptr;
+    unsigned long long *keys_base[2] = {nullptr, nullptr};
+    uint32_t *rgba_base = nullptr;
+    mmr::CloudDev *d_clouds = nullptr;
+    mmr::Cam *d_cams = nullptr;
+    uint2 *d_point_chunks = nullptr;
+    uint2 *d_pixel_chunks = nullptr;
+    uint64_t point_chunk_bytes = 0, pixel_chunk_bytes = 0;
+    uint32_t n_point_chunks = 0, n_pixel_chunks = 0;
+    uint32_t *d_frame = nullptr;
+
+    std::vector<mmr::Cam> cams;      // host copy [slots][count]
+    std::vector<uint8_t> cam_set;
+    mmr::Cam *staging = nullptr;     // pinned staging for camera uploads
+    cudaEvent_t staging_done = nullptr;
+    bool cams_dirty = false;
+
+    uint32_t frames = 0;             // frames enqueued
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+
+    char err[512] = "";
+};
+
+namespace {
+
+thread_local char g_batch_error[512] = "";
+
+mmr_status bfail(mmr_batch *b, mmr_status s, const char *fmt, ...)
+{
+    char *dst = b ? b->err : g_batch_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+mmr_status bcuda(mmr_batch *b, cudaError_t e, const char *what)
+{
+    return bfail(b, MMR_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+mmr_status balloc(mmr_batch *b, void **p, uint64_t bytes, const char *what)
+{
+    *p = nullptr;
+    if (b->budget && b->held + bytes > b->budget)
+        return bfail(b, MMR_ERR_BUDGET, "%s: %llu bytes would exceed the budget (%llu of %llu held)", what,
+                     (unsigned long long)bytes, (unsigned long long)b->held, (unsigned long long)b->budget);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return bfail(b, e == cudaErrorMemoryAllocation ? MMR_ERR_OOM : MMR_ERR_CUDA, "%s: cudaMalloc(%llu): %s",
+                     what, (unsigned long long)bytes, cudaGetErrorString(e));
+    }
+    b->held += bytes;
+    return MMR_OK;
+}
+
+void bfree(mmr_batch *b, void **p, uint64_t bytes)
+{
+    if (*p) {
+        cudaFree(*p);
+        b->held -= bytes;
+        *p = nullptr;
+    }
+}
+
+uint64_t point_bytes(uint64_t n, int dtype) { return n * (dtype == MMR_F32x3 ? 12u : 6u); }
+
+uint32_t groups_for(uint64_t n, int dtype)
+{
+    const uint64_t g = dtype == MMR_F32x3 ? 4 : 8;
+    return (uint32_t)((n + g - 1) / g);
+}
+
+uint32_t chunk_quads(const mmr_batch *b) { return 4u * b->chunk_groups; }
+
+// (Re)build the point and pixel chunk tables for the current chunk size.
+mmr_status build_chunks(mmr_batch *b)
+{
+    std::vector<uint2> pc, xc;
+    const uint32_t cq = chunk_quads(b);
+    for (int c = 0; c < b->count; ++c) {
+        const uint32_t groups = groups_for(b->desc[c].n, b->dtype);
+        for (uint32_t g = 0; g < groups; g += b->chunk_groups)
+            pc.push_back(make_uint2((uint32_t)c, g));
+        const uint32_t quads = (uint32_t)(((uint64_t)b->desc[c].width * b->desc[c].height) / 4);
+        uint32_t q = 0;
+        do {                          // at least one chunk per cloud: it owns the ragged tail
+            xc.push_back(make_uint2((uint32_t)c, q));
+            q += cq;
+        } while (q < quads);
+    }
+    bfree(b, (void **)&b->d_point_chunks, b->point_chunk_bytes);
+    bfree(b, (void **)&b->d_pixel_chunks, b->pixel_chunk_bytes);
+    b->point_chunk_bytes = pc.size() * sizeof(uint2);
+    b->pixel_chunk_bytes = xc.size() * sizeof(uint2);
+    mmr_status st = balloc(b, (void **)&b->d_point_chunks, b->point_chunk_bytes, "point chunk table");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->d_pixel_chunks, b->pixel_chunk_bytes, "pixel chunk table");
+    if (st != MMR_OK)
+        return st;
+    cudaError_t e = cudaMemcpy(b->d_point_chunks, pc.data(), b->point_chunk_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_pixel_chunks, xc.data(), b->pixel_chunk_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return bcuda(b, e, "chunk table upload");
+    b->n_point_chunks = (uint32_t)pc.size();
+    b->n_pixel_chunks = (uint32_t)xc.size();
+    return MMR_OK;
+}
+
+mmr::BatchTables tables(const mmr_batch *b)
+{
+    mmr::BatchTables T;
+    T.clouds = b->d_clouds;
+    T.cams = b->d_cams;
+    T.point_chunks = b->d_point_chunks;
+    T.pixel_chunks = b->d_pixel_chunks;
+    T.n_point_chunks = b->n_point_chunks;
+    T.n_pixel_chunks = b->n_pixel_chunks;
+    T.chunk_groups = b->chunk_groups;
+    T.chunk_quads = chunk_quads(b);
+    T.count = (uint32_t)b->count;
+    T.slots = (uint32_t)b->slots;
+    T.first_step = 0;
+    T.frame = b->d_frame;
+    return T;
+}
+
+mmr_status upload_cameras(mmr_batch *b, cudaStream_t s)
+{
+    if (!b->cams_dirty)
+        return MMR_OK;
+    cudaError_t e = cudaEventSynchronize(b->staging_done);   // previous upload has left the staging buffer
+    if (e != cudaSuccess)
+        return bcuda(b, e, "camera staging wait");
+    memcpy(b->staging, b->cams.data(), b->cams.size() * sizeof(mmr::Cam));
+    e = cudaMemcpyAsync(b->d_cams, b->staging, b->cams.size() * sizeof(mmr::Cam), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(b->staging_done, s);
+    if (e != cudaSuccess)
+        return bcuda(b, e, "camera upload");
+    b->cams_dirty = false;
+    return MMR_OK;
+}
+
+int grid_for(const mmr_batch *b, uint32_t chunks)
+{
+    if (b->launch.ctas_per_sm > 0)
+        return std::max(1, std::min<int>(b->launch.sm_count * b->launch.ctas_per_sm, (int)std::max(1u, chunks)));
+    return (int)std::max(1u, chunks);
+}
+
+// Enqueue one frame (three kernels) on s; no host synchronisation.
+cudaError_t enqueue_frame(const mmr_batch *b, cudaStream_t s)
+{
+    const mmr::BatchTables T = tables(b);
+    const int gp = grid_for(b, b->n_point_chunks);
+    switch (b->dtype) {
+    case MMR_F32x3: mmr::batch_points_kernel<mmr::kF32><<<gp, b->launch.threads, 0, s>>>(T); break;
+    case MMR_F16x3: mmr::batch_points_kernel<mmr::kF16><<<gp, b->launch.threads, 0, s>>>(T); break;
+    default: mmr::batch_points_kernel<mmr::kBF16><<<gp, b->launch.threads, 0, s>>>(T); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    mmr::batch_resolve_kernel<<<grid_for(b, b->n_pixel_chunks), b->launch.threads, 0, s>>>(T);
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    mmr::batch_advance_kernel<<<1, 1, 0, s>>>(b->d_frame);
+    return cudaGetLastError();
+}
+
+mmr_status cameras_ready(mmr_batch *b, bool all_slots)
+{
+    const int first = all_slots ? 0 : (int)(b->frames % (uint32_t)b->slots);
+    const int last = all_slots ? b->slots : first + 1;
+    for (int s = first; s < last; ++s)
+        for (int c = 0; c < b->count; ++c)
+            if (!b->cam_set[(size_t)s * b->count + c])
+                return bfail(b, MMR_ERR_STATE, "camera of cloud %d, slot %d not set", c, s);
+    return MMR_OK;
+}
+
+void drop_graph(mmr_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mmr_batch_last_error(const mmr_batch *b) { return b ? b->err : g_batch_error; }
+
+mmr_status mmr_batch_destroy(mmr_batch *b)
+{
+    if (!b)
+        return MMR_OK;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    bfree(b, &b->pos_base, b->pos_bytes);
+    bfree(b, (void **)&b->keys_base[0], b->total_px * 8);
+    bfree(b, (void **)&b->keys_base[1], b->total_px * 8);
+    bfree(b, (void **)&b->rgba_base, b->total_px * 4);
+    bfree(b, (void **)&b->d_clouds, (uint64_t)b->count * sizeof(mmr::CloudDev));
+    bfree(b, (void **)&b->d_cams, b->cams.size() * sizeof(mmr::Cam));
+    bfree(b, (void **)&b->d_point_chunks, b->point_chunk_bytes);
+    bfree(b, (void **)&b->d_pixel_chunks, b->pixel_chunk_bytes);
+    bfree(b, (void **)&b->d_frame, 4);
+    if (b->staging)
+        cudaFreeHost(b->staging);
+    if (b->staging_done)
+        cudaEventDestroy(b->staging_done);
+    if (b->capture_stream)
+        cudaStreamDestroy(b->capture_stream);
+    delete b;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, int camera_slots,
+                            uint64_t budget_bytes, mmr_batch **out)
+{
+    if (!out || !clouds)
+        return bfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_batch_create: NULL argument");
+    *out = nullptr;
+    if (count < 1 || count > 65536 || camera_slots < 1 || camera_slots > 4096)
+        return bfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_batch_create: count %d or camera_slots %d out of range",
+                     count, camera_slots);
+    if (dtype != MMR_F32x3 && dtype != MMR_F16x3 && dtype != MMR_BF16x3)
+        return bfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_batch_create: unknown dtype %d", dtype);
+    for (int c = 0; c < count; ++c) {
+        const mmr_cloud_desc &d = clouds[c];
+        if (d.n == 0 || d.n >= (1ull << 32) || d.width < 1 || d.height < 1 || d.width > 32768 ||
+            d.height > 32768 || !(d.amplitude >= 0.0f && d.amplitude <= 1.0f))
+            return bfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_batch_create: cloud %d has an invalid descriptor", c);
+    }
+    mmr_batch *b = new (std::nothrow) mmr_batch();
+    if (!b)
+        return bfail(nullptr, MMR_ERR_OOM, "mmr_batch_create: host allocation failed");
+    b->count = count;
+    b->dtype = dtype;
+    b->slots = camera_slots;
+    b->budget = budget_bytes;
+    b->desc.assign(clouds, clouds + count);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&b->launch.sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bfail(nullptr, MMR_ERR_CUDA, "mmr_batch_create: no usable CUDA device: %s", cudaGetErrorString(e));
+        delete b;
+        return MMR_ERR_CUDA;
+    }
+    b->launch.threads = 256;
+    b->launch.ctas_per_sm = 4;
+    // layout: positions 256-byte aligned per cloud and padded to 48-byte groups
+    for (int c = 0; c < count; ++c) {
+        b->pos_off.push_back(b->pos_bytes);
+        const uint64_t bytes = (point_bytes(clouds[c].n, dtype) + 47) / 48 * 48;
+        b->pos_bytes += (bytes + 255) / 256 * 256;
+        b->px_off.push_back(b->total_px);
+        const uint64_t px = (uint64_t)clouds[c].width * clouds[c].height;
+        b->total_px += (px + 31) / 32 * 32;             // keeps every framebuffer 256-byte aligned
+    }
+    b->cams.assign((size_t)camera_slots * count, mmr::Cam{});
+    b->cam_set.assign((size_t)camera_slots * count, 0);
+    mmr_status st = balloc(b, &b->pos_base, b->pos_bytes, "batch positions");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->keys_base[0], b->total_px * 8, "batch depth-id buffers 0");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->keys_base[1], b->total_px * 8, "batch depth-id buffers 1");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->rgba_base, b->total_px * 4, "batch framebuffers");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->d_clouds, (uint64_t)count * sizeof(mmr::CloudDev), "cloud table");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->d_cams, b->cams.size() * sizeof(mmr::Cam), "camera table");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->d_frame, 4, "frame counter");
+    if (st == MMR_OK)
+        st = build_chunks(b);
+    if (st == MMR_OK) {
+        std::vector<mmr::CloudDev> host(count);
+        for (int c = 0; c < count; ++c) {
+            const mmr_cloud_desc &d = clouds[c];
+            mmr::CloudDev &h = host[c];
+            h.pos = (char *)b->pos_base + b->pos_off[c];
+            h.keys[0] = b->keys_base[0] + b->px_off[c];
+            h.keys[1] = b->keys_base[1] + b->px_off[c];
+            h.rgba = b->rgba_base + b->px_off[c];
+            h.n = (uint32_t)d.n;
+            h.npx = (uint32_t)((uint64_t)d.width * d.height);
+            h.W = d.width;
+            h.H = d.height;
+            h.fW = (float)d.width;
+            h.fH = (float)d.height;
+            h.halfW = 0.5f * (float)d.width;
+            h.halfH = 0.5f * (float)d.height;
+            h.seed_lo = (uint32_t)(d.seed & 0xffffffffu);
+            h.seed_hi = (uint32_t)(d.seed >> 32);
+            h.cloud = d.cloud;
+            h.amplitude = d.amplitude;
+            h.color = d.color;
+            h.background = d.background;
+        }
+        e = cudaMemcpy(b->d_clouds, host.data(), host.size() * sizeof(mmr::CloudDev), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemset(b->pos_base, 0, b->pos_bytes);
+        if (e == cudaSuccess)
+            e = cudaMemset(b->keys_base[0], 0xff, b->total_px * 8);
+        if (e == cudaSuccess)
+            e = cudaMemset(b->keys_base[1], 0xff, b->total_px * 8);
+        if (e == cudaSuccess)
+            e = cudaMemset(b->rgba_base, 0, b->total_px * 4);
+        if (e == cudaSuccess)
+            e = cudaMemset(b->d_frame, 0, 4);
+        if (e == cudaSuccess)
+            e = cudaMallocHost((void **)&b->staging, b->cams.size() * sizeof(mmr::Cam));
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&b->staging_done, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaDeviceSynchronize();
+        if (e != cudaSuccess)
+            st = bcuda(b, e, "mmr_batch_create: set-up");
+    }
+    if (st != MMR_OK) {
+        snprintf(g_batch_error, sizeof g_batch_error, "%s", b->err);
+        mmr_batch_destroy(b);
+        return st;
+    }
+    g_batch_error[0] = 0;
+    *out = b;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_points(mmr_batch *b, int cloud, void **dev_ptr)
+{
+    if (!b || !dev_ptr || cloud < 0 || cloud >= (b ? b->count : 0))
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_points: bad argument");
+    *dev_ptr = (char *)b->pos_base + b->pos_off[cloud];
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_set_camera(mmr_batch *b, int cloud, int slot, const double eye[3], const double target[3],
+                                const double up[3], double fovy_deg, double znear, double zfar)
+{
+    if (!b || !eye || !target || !up || cloud < 0 || cloud >= b->count || slot < 0 || slot >= b->slots)
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_camera: bad argument");
+    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar))
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_camera: need 0 < fovy < 180, 0 < znear < zfar");
+    float m[16];
+    const double aspect = (double)b->desc[cloud].width / (double)b->desc[cloud].height;
+    if (!mmr::build_clip_matrix(eye, target, up, fovy_deg, aspect, znear, zfar, m))
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_camera: eye == target or up parallel to view");
+    mmr::Cam &cam = b->cams[(size_t)slot * b->count + cloud];
+    for (int k = 0; k < 4; ++k) {
+        cam.rx[k] = m[k];
+        cam.ry[k] = m[4 + k];
+        cam.rw[k] = m[12 + k];
+    }
+    cam.znear = (float)znear;
+    cam.zfar = (float)zfar;
+    b->cam_set[(size_t)slot * b->count + cloud] = 1;
+    b->cams_dirty = true;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_sm, int chunk_groups)
+{
+    if (!b)
+        return MMR_ERR_INVALID_ARG;
+    if (threads < 32 || threads > mmr::kBatchMaxThreads || threads % 32 || ctas_per_sm < 0 || ctas_per_sm > 64 ||
+        chunk_groups < 1 || chunk_groups > 65536)
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_launch: out of range");
+    const bool rechunk = (uint32_t)chunk_groups != b->chunk_groups;
+    b->launch.threads = threads;
+    b->launch.ctas_per_sm = ctas_per_sm;
+    b->chunk_groups = (uint32_t)chunk_groups;
+    drop_graph(b);
+    if (rechunk) {
+        cudaError_t e = cudaDeviceSynchronize();     // old tables may still be in use
+        if (e != cudaSuccess)
+            return bcuda(b, e, "mmr_batch_set_launch: sync");
+        return build_chunks(b);
+    }
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream)
+{
+    if (!b)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = cameras_ready(b, false);
+    if (st != MMR_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = upload_cameras(b, s);
+    if (st != MMR_OK)
+        return st;
+    cudaError_t e = enqueue_frame(b, s);
+    if (e != cudaSuccess)
+        return bcuda(b, e, "batch frame launch");
+    b->frames += 1;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_run_graph(mmr_batch *b, int frames, void *stream)
+{
+    if (!b || frames < 0)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = cameras_ready(b, true);
+    if (st != MMR_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = upload_cameras(b, s);
+    if (st != MMR_OK)
+        return st;
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess)
+            return bcuda(b, e, "graph capture begin");
+        cudaError_t le = enqueue_frame(b, b->capture_stream);
+        e = cudaStreamEndCapture(b->capture_stream, &g);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (g)
+                cudaGraphDestroy(g);
+            return bcuda(b, le != cudaSuccess ? le : e, "graph capture");
+        }
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return bcuda(b, e, "graph instantiate");
+        }
+    }
+    for (int f = 0; f < frames; ++f) {
+        cudaError_t e = cudaGraphLaunch(b->graph, s);
+        if (e != cudaSuccess)
+            return bcuda(b, e, "graph launch");
+        b->frames += 1;
+    }
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config, int *threads, int *ctas_per_sm,
+                              int *chunk_groups, float *best_ms)
+{
+    if (!b || frames_per_config < 1 || frames_per_config > 1000)
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_autotune: bad argument");
+    mmr_status st = cameras_ready(b, true);
+    if (st != MMR_OK)
+        return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *saved = nullptr;
+    st = balloc(b, &saved, b->pos_bytes, "autotune position snapshot");
+    if (st != MMR_OK)
+        return st;
+    const uint32_t saved_frames = b->frames;
+    const mmr::LaunchShape saved_launch = b->launch;
+    const uint32_t saved_chunk = b->chunk_groups;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(saved, b->pos_base, b->pos_bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&t1);
+    st = e == cudaSuccess ? upload_cameras(b, s) : bcuda(b, e, "autotune set-up");
+    const int cand_threads[] = {128, 256, 512};
+    const int cand_ctas[] = {0, 1, 2, 4, 8};
+    const int cand_chunk[] = {64, 256, 1024};
+    float best = 1e30f;
+    int bt = saved_launch.threads, bc = saved_launch.ctas_per_sm, bg = (int)saved_chunk;
+    for (int cg : cand_chunk) {
+        if (st != MMR_OK)
+            break;
+        for (int th : cand_threads) {
+            if (st != MMR_OK)
+                break;
+            for (int ct : cand_ctas) {
+                st = mmr_batch_set_launch(b, th, ct, cg);
+                if (st != MMR_OK)
+                    break;
+                e = enqueue_frame(b, s);                         // warm-up frame
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(t0, s);
+                for (int f = 0; f < frames_per_config && e == cudaSuccess; ++f)
+                    e = enqueue_frame(b, s);
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(t1, s);
+                if (e == cudaSuccess)
+                    e = cudaEventSynchronize(t1);
+                float ms = 0.0f;
+                if (e == cudaSuccess)
+                    e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) {
+                    st = bcuda(b, e, "autotune timing");
+                    break;
+                }
+                ms /= (float)frames_per_config;
+                if (ms < best) {
+                    best = ms;
+                    bt = th;
+                    bc = ct;
+                    bg = cg;
+                }
+            }
+        }
+    }
+    // restore the simulation state whatever happened above
+    cudaError_t re = cudaMemcpyAsync(b->pos_base, saved, b->pos_bytes, cudaMemcpyDeviceToDevice, s);
+    if (re == cudaSuccess)
+        re = cudaMemsetAsync(b->keys_base[0], 0xff, b->total_px * 8, s);
+    if (re == cudaSuccess)
+        re = cudaMemsetAsync(b->keys_base[1], 0xff, b->total_px * 8, s);
+    if (re == cudaSuccess)
+        re = cudaMemsetAsync(b->rgba_base, 0, b->total_px * 4, s);
+    if (re == cudaSuccess)
+        re = cudaStreamSynchronize(s);
+    if (re == cudaSuccess)
+        re = cudaMemcpy(b->d_frame, &saved_frames, 4, cudaMemcpyHostToDevice);
+    b->frames = saved_frames;
+    bfree(b, &saved, b->pos_bytes);
+    if (t0)
+        cudaEventDestroy(t0);
+    if (t1)
+        cudaEventDestroy(t1);
+    if (re != cudaSuccess)
+        return bcuda(b, re, "autotune restore");
+    if (st != MMR_OK) {
+        mmr_batch_set_launch(b, saved_launch.threads, saved_launch.ctas_per_sm, (int)saved_chunk);
+        return st;
+    }
+    st = mmr_batch_set_launch(b, bt, bc, bg);
+    if (st != MMR_OK)
+        return st;
+    if (threads)
+        *threads = bt;
+    if (ctas_per_sm)
+        *ctas_per_sm = bc;
+    if (chunk_groups)
+        *chunk_groups = bg;
+    if (best_ms)
+        *best_ms = best;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t **rgba, const uint64_t **depth_id)
+{
+    if (!b || cloud < 0 || cloud >= b->count)
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_frame_ptr: bad argument");
+    const int latest = b->frames ? (int)((b->frames - 1) & 1u) : 1;
+    if (rgba)
+        *rgba = b->rgba_base + b->px_off[cloud];
+    if (depth_id)
+        *depth_id = reinterpret_cast<const uint64_t *>(b->keys_base[latest] + b->px_off[cloud]);
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_frames(const mmr_batch *b, uint32_t *frames)
+{
+    if (!b || !frames)
+        return MMR_ERR_INVALID_ARG;
+    *frames = b->frames;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_device_bytes(const mmr_batch *b, uint64_t *bytes)
+{
+    if (!b || !bytes)
+        return MMR_ERR_INVALID_ARG;
+    *bytes = b->held;
+    return MMR_OK;
+}
+
+}  // extern "C"
