@@ -248,6 +248,45 @@ MMR_API mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t *
 MMR_API mmr_status mmr_batch_frames(const mmr_batch *b, uint32_t *frames);
 MMR_API mmr_status mmr_batch_device_bytes(const mmr_batch *b, uint64_t *bytes);
 
+/* ---- rendering without allocation ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc.  Examples: a simulation embedded in a host
+ * program whose own memory manager owns the device (a pool or arena that
+ * every allocation must go through, with the rest of memory reserved), or a
+ * real-time loop that must not allocate per frame because an allocation can
+ * synchronise the device and stall it.  Such a caller keeps its positions
+ * and its RGBA8 output in memory it already owns and passes both in; the
+ * only scratch this call needs, the per-pixel depth-id keys, lives in a
+ * fixed-size array inside the library.
+ *
+ * MMR_STATIC_MAX_PIXELS: capacity of that array, in pixels (8 bytes each,
+ * 32 MiB).  Every GPU on which the library is loaded holds the array until
+ * the process exits, whether or not this function is called.
+ *
+ * mmr_render_static: render n points (dtype as mmr_alloc_points; dev_points
+ * 16-byte aligned, n*3 coordinates, AoS, read only) with the FP32 row-major
+ * clip matrix m (rows x, y and w used; znear < clip w < zfar drawn) into
+ * dev_rgba (width*height uint32 RGBA8, row 0 at the top, written): each
+ * covered pixel gets `color`, the others `background`.  The frame equals
+ * what mmr_set_matrix + mmr_render produce for the same points.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or other allocating call.
+ *  - width*height above MMR_STATIC_MAX_PIXELS, n outside 1..2^32-1, a NULL
+ *    pointer or a misaligned dev_points: MMR_ERR_INVALID_ARG, nothing launched.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address once; make that first call before any CUDA
+ *    stream capture that contains this call.
+ *  - Every call on a device shares the one array.  Each call clears the
+ *    part it uses before drawing, but calls whose work overlaps on the GPU
+ *    (different streams, or threads without ordering between them) race on
+ *    it and give wrong frames: order them on one stream.
+ *  - Work is enqueued on `stream` (NULL = legacy default stream); the
+ *    frame is complete when the stream is synchronised.  Errors are read
+ *    with mmr_last_error(NULL). */
+#define MMR_STATIC_MAX_PIXELS 4194304u
+MMR_API mmr_status mmr_render_static(const void *dev_points, uint64_t n, int dtype, const float m[16],
+                                     float znear, float zfar, int width, int height, uint32_t color,
+                                     uint32_t background, uint32_t *dev_rgba, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

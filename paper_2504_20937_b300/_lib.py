@@ -77,6 +77,9 @@ SIGNATURES.update({
     "mmr_batch_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
 })
 
+SIGNATURES["mmr_render_static"] = (_i, [_vp, _u64, _i, _f16, _f, _f, _i, _i, _u32, _u32, _vp, _vp])
+STATIC_MAX_PIXELS = 4194304
+
 _lib = None
 
 

@@ -190,6 +190,8 @@ mmr_status frame(mmr_ctx *c, void *pos, bool displace, cudaStream_t s)
 
 namespace mmr {
 
+void set_process_error(const char *msg) { snprintf(g_create_error, sizeof g_create_error, "%s", msg); }
+
 bool build_clip_matrix(const double eye[3], const double target[3], const double up[3],
                        double fovy_deg, double aspect, double znear, double zfar, float out[16])
 {

@@ -21,6 +21,9 @@ cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *n
                            uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,
                            uint32_t background, const LaunchShape &ls, cudaStream_t s);
 
+// Message returned by mmr_last_error(NULL) on this thread.
+void set_process_error(const char *msg);
+
 // FP64 camera -> FP32 clip matrix (row-major 4x4); returns false on invalid input.
 bool build_clip_matrix(const double eye[3], const double target[3], const double up[3],
                        double fovy_deg, double aspect, double znear, double zfar, float out[16]);
