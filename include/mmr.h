@@ -124,10 +124,19 @@ MMR_API mmr_status mmr_set_sim(mmr_ctx *ctx, uint64_t seed, uint32_t cloud, floa
 /* Default point colour (no colour buffer) and background colour, RGBA8. */
 MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background);
 
-/* Kernel launch shape: threads per block (a multiple of 32, 32..1024) and
- * CTAs per SM for the point kernel's grid (0 = one thread per point group).
- * Results do not depend on it; only speed does. */
-MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm);
+/* Kernel launch shape of the point kernel.
+ *  kernel = MMR_KERNEL_GRID: grid-stride over 48-byte point groups with
+ *    `threads` per block (a multiple of 32, 32..1024); ctas_per_sm = 0 gives
+ *    one thread per group, ctas_per_sm > 0 a persistent grid of
+ *    sm_count * ctas_per_sm CTAs in which every thread prefetches its next
+ *    group while working on the current one.
+ *  kernel = MMR_KERNEL_TMA: persistent, TMA-staged (threads 128, 256 or
+ *    512; ctas_per_sm >= 1): each CTA keeps 4 tiles of threads*48 bytes in
+ *    flight through shared memory with bulk copies.
+ * Results never depend on the shape; only speed does.  The default is the
+ * fastest shape measured on B300 (see the library's design notes). */
+enum mmr_kernel { MMR_KERNEL_GRID = 0, MMR_KERNEL_TMA = 1 };
+MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel);
 
 /* ---- frames ---------------------------------------------------------------- */
 
@@ -169,6 +178,11 @@ MMR_API mmr_status mmr_get_step(const mmr_ctx *ctx, uint32_t *step);
  * NULL).  MMR_ERR_STATE if timing is off or no frame was timed yet. */
 MMR_API mmr_status mmr_set_timing(mmr_ctx *ctx, int enable);
 MMR_API mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *resolve_ms);
+
+/* Synchronise the device and report whether a kernel of this context gave
+ * up a bounded wait (MMR_ERR_TIMEOUT; the flag is then cleared) since the
+ * last check.  A timed-out frame is incomplete; the context stays usable. */
+MMR_API mmr_status mmr_check_device(mmr_ctx *ctx);
 
 /* Device bytes this context holds right now. */
 MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);

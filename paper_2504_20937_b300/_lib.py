@@ -41,7 +41,7 @@ SIGNATURES = {
     "mmr_get_matrix": (_i, [_vp, _f16]),
     "mmr_set_sim": (_i, [_vp, _u64, _u32, _f, _u32]),
     "mmr_set_style": (_i, [_vp, _u32, _u32]),
-    "mmr_set_launch": (_i, [_vp, _i, _i]),
+    "mmr_set_launch": (_i, [_vp, _i, _i, _i]),
     "mmr_step_and_render": (_i, [_vp, _vp]),
     "mmr_displace": (_i, [_vp, _vp]),
     "mmr_render": (_i, [_vp, _vp]),
@@ -49,6 +49,7 @@ SIGNATURES = {
     "mmr_frame_ptr": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
     "mmr_get_step": (_i, [_vp, C.POINTER(_u32)]),
     "mmr_set_timing": (_i, [_vp, _i]),
+    "mmr_check_device": (_i, [_vp]),
     "mmr_last_kernel_ms": (_i, [_vp, C.POINTER(_f), C.POINTER(_f)]),
     "mmr_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
 }

@@ -109,8 +109,10 @@ class Context:
     def set_style(self, color: int = 0xFFFFFFFF, background: int = 0):
         self._check(self._lib.mmr_set_style(self._h, color, background))
 
-    def set_launch(self, threads: int = 256, ctas_per_sm: int = 0):
-        self._check(self._lib.mmr_set_launch(self._h, threads, ctas_per_sm))
+    def set_launch(self, threads: int = 256, ctas_per_sm: int = 0, kernel: int = 0):
+        """kernel 0: grid-stride (ctas_per_sm 0 = one thread per group, else
+        persistent with prefetch); kernel 1: TMA-staged persistent."""
+        self._check(self._lib.mmr_set_launch(self._h, threads, ctas_per_sm, kernel))
 
     # -- frames
     def step_and_render(self, stream=None):
@@ -139,6 +141,10 @@ class Context:
         """int64[H, W] view of the latest depth-id keys (reinterpret as uint64)."""
         _, k = self.frame_ptrs()
         return device_view(k, (self.H, self.W), "<i8")
+
+    def check_device(self):
+        """Raise MmrError(MMR_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
+        self._check(self._lib.mmr_check_device(self._h))
 
     def set_timing(self, enable: bool = True):
         self._check(self._lib.mmr_set_timing(self._h, int(enable)))

@@ -29,6 +29,7 @@ struct mmr_ctx {
     int splat_buf = 0;            // key buffer the next frame splats into
     int latest_buf = 0;           // key buffer holding the latest frame
     uint32_t *rgba = nullptr;
+    uint32_t *d_err = nullptr;    // device error word (bounded waits that gave up)
 
     void *points = nullptr;
     uint64_t n = 0;
@@ -146,6 +147,7 @@ mmr::PointParams point_params(const mmr_ctx *c)
     P.cloud = c->cloud;
     P.amplitude = c->amplitude;
     P.id_base = 0;
+    mmr::philox_prepare(P);
     return P;
 }
 
@@ -158,6 +160,18 @@ mmr_status check_frame_ready(mmr_ctx *c, bool need_cam)
     return MMR_OK;
 }
 
+bool uses_tma(const mmr::LaunchShape &ls) { return ls.kernel == MMR_KERNEL_TMA; }
+
+// The TMA-staged persistent kernel when the launch shape allows it (the
+// context's buffers are padded to whole groups), else the grid-stride one.
+cudaError_t launch_point_kernel(mmr_ctx *c, void *pos, const mmr::PointParams &P, bool displace, bool splat,
+                                cudaStream_t s)
+{
+    if (uses_tma(c->launch))
+        return mmr::launch_points_tma(c->dtype, pos, (uint32_t)c->n, P, displace, splat, c->d_err, c->launch, s);
+    return mmr::launch_points(c->dtype, pos, (uint32_t)c->n, P, displace, splat, c->launch, s);
+}
+
 // Render the current point buffer `pos` into the splat key buffer, then
 // resolve and flip buffers.  `displace` fuses the step into the same kernel.
 mmr_status frame(mmr_ctx *c, void *pos, bool displace, cudaStream_t s)
@@ -165,7 +179,7 @@ mmr_status frame(mmr_ctx *c, void *pos, bool displace, cudaStream_t s)
     mmr::PointParams P = point_params(c);
     if (c->timing)
         cudaEventRecord(c->ev[0], s);
-    cudaError_t e = mmr::launch_points(c->dtype, pos, (uint32_t)c->n, P, displace, true, c->launch, s);
+    cudaError_t e = launch_point_kernel(c, pos, P, displace, true, s);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "point kernel launch");
     if (c->timing)
@@ -270,6 +284,9 @@ mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx *
     c->W = width;
     c->H = height;
     c->budget = budget_bytes;
+    c->launch.threads = 128;          // fastest measured shape (grid-stride, one thread per group)
+    c->launch.ctas_per_sm = 0;
+    c->launch.kernel = MMR_KERNEL_GRID;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&c->launch.sm_count, cudaDevAttrMultiProcessorCount, c->device);
@@ -285,8 +302,12 @@ mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx *
         st = dev_alloc(c, (void **)&c->keys[1], npx * 8, "depth-id buffer 1");
     if (st == MMR_OK)
         st = dev_alloc(c, (void **)&c->rgba, npx * 4, "RGBA framebuffer");
+    if (st == MMR_OK)
+        st = dev_alloc(c, (void **)&c->d_err, 4, "device error word");
     if (st == MMR_OK) {
-        e = cudaMemset(c->keys[0], 0xff, npx * 8);
+        e = cudaMemset(c->d_err, 0, 4);
+        if (e == cudaSuccess)
+            e = cudaMemset(c->keys[0], 0xff, npx * 8);
         if (e == cudaSuccess)
             e = cudaMemset(c->keys[1], 0xff, npx * 8);
         if (e == cudaSuccess)
@@ -316,6 +337,7 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     dev_free(ctx, (void **)&ctx->keys[0], frame_px(ctx) * 8);
     dev_free(ctx, (void **)&ctx->keys[1], frame_px(ctx) * 8);
     dev_free(ctx, (void **)&ctx->rgba, frame_px(ctx) * 4);
+    dev_free(ctx, (void **)&ctx->d_err, 4);
     dev_free(ctx, &ctx->points, storage_bytes(ctx->n, ctx->dtype));
     dev_free(ctx, (void **)&ctx->colors, ctx->n * 4);
     dev_free(ctx, &ctx->rt_device, storage_bytes(ctx->n, ctx->dtype));
@@ -449,15 +471,21 @@ mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background)
     return MMR_OK;
 }
 
-mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm)
+mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel)
 {
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     if (threads < 32 || threads > 1024 || threads % 32 != 0 || ctas_per_sm < 0 || ctas_per_sm > 64)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: threads %d / ctas_per_sm %d out of range",
                     threads, ctas_per_sm);
+    if (kernel != MMR_KERNEL_GRID && kernel != MMR_KERNEL_TMA)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: unknown kernel %d", kernel);
+    if (kernel == MMR_KERNEL_TMA && (ctas_per_sm < 1 || (threads != 128 && threads != 256 && threads != 512)))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: the TMA kernel needs 128/256/512 threads and "
+                    "ctas_per_sm >= 1");
     ctx->launch.threads = threads;
     ctx->launch.ctas_per_sm = ctas_per_sm;
+    ctx->launch.kernel = kernel;
     return MMR_OK;
 }
 
@@ -489,8 +517,7 @@ mmr_status mmr_displace(mmr_ctx *ctx, void *stream)
     if (st != MMR_OK)
         return st;
     mmr::PointParams P = point_params(ctx);
-    cudaError_t e = mmr::launch_points(ctx->dtype, ctx->points, (uint32_t)ctx->n, P, true, false,
-                                       ctx->launch, (cudaStream_t)stream);
+    cudaError_t e = launch_point_kernel(ctx, ctx->points, P, true, false, (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "displace kernel launch");
     ctx->step += 1;
@@ -602,6 +629,23 @@ mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *resolve_ms)
         *point_ms = a;
     if (resolve_ms)
         *resolve_ms = b;
+    return MMR_OK;
+}
+
+mmr_status mmr_check_device(mmr_ctx *ctx)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    uint32_t word = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&word, ctx->d_err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_check_device");
+    if (word) {
+        cudaMemset(ctx->d_err, 0, 4);
+        return fail(ctx, MMR_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy (error word %u)", word);
+    }
     return MMR_OK;
 }
 

@@ -85,10 +85,20 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_points_kernel(BatchTab
         P.cloud = cl.cloud;
         P.amplitude = cl.amplitude;
         P.id_base = 0;
+        philox_prepare(P);
         const uint32_t n = cl.n;
         const uint32_t end = min(ch.y + T.chunk_groups, groups_of<DT>(n));
-        for (uint32_t g = ch.y + threadIdx.x; g < end; g += blockDim.x)
-            process_group<DT, true, true>(cl.pos, n, g, P);
+        const uint32_t full = n / Group<DT>::kPoints;
+        for (uint32_t g = ch.y + threadIdx.x; g < end; g += blockDim.x) {
+            if (g < full) {
+                uint4 q[3];
+                load_words(cl.pos, g, q);
+                process_words<DT, true, true>(q, g * Group<DT>::kPoints, Group<DT>::kPoints, P);
+                store_words(cl.pos, g, q);
+            } else {
+                process_tail<DT, true, true>(cl.pos, n, g * Group<DT>::kPoints, P);
+            }
+        }
     }
 }
 

@@ -12,10 +12,17 @@ struct LaunchShape {
     int threads = 256;       // threads per block
     int ctas_per_sm = 0;     // 0: one thread per work item; else a persistent grid
     int sm_count = 148;
+    int kernel = 0;          // 0: grid-stride point kernel, 1: TMA-staged
 };
 
 cudaError_t launch_points(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
                           bool splat, const LaunchShape &ls, cudaStream_t s);
+
+// TMA-staged persistent variant (threads 128, 256 or 512; grid =
+// sm_count * ctas_per_sm CTAs).  The buffer must be padded to whole 48-byte
+// groups.  A timed-out wait sets *err (device word) to a non-zero value.
+cudaError_t launch_points_tma(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
+                              uint32_t *err, const LaunchShape &ls, cudaStream_t s);
 
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys,
                            uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,

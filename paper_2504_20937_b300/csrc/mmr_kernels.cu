@@ -1,22 +1,149 @@
 // Kernels of the single-cloud path: fused displace + project + splat over the
 // points (grid-stride over 48-byte point groups), and resolve + clear over
 // the pixels.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "mmr_device.cuh"
 #include "mmr_internal.h"
 #include "mmr_points.cuh"
 #include "mmr_resolve.cuh"
+#include "mmr_tma.cuh"
 
 namespace mmr {
 
+// Grid-stride over 48-byte point groups.  With a persistent grid (fewer
+// threads than groups) each thread prefetches its next group into registers
+// before working on the current one, so a load is always in flight while the
+// thread computes; with one thread per group the loop runs once.
 template <int DT, bool kDisplace, bool kSplat>
 __global__ void points_kernel(void *__restrict__ pos, uint32_t n, PointParams P)
 {
+    constexpr int G = Group<DT>::kPoints;
+    const uint32_t full = n / G;
     const uint32_t groups = groups_of<DT>(n);
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride)
-        process_group<DT, kDisplace, kSplat>(pos, n, g, P);
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    uint4 next[3];
+    if (g < full)
+        load_words(pos, g, next);
+    while (g < groups) {
+        const uint32_t gn = g + stride;
+        if (g < full) {
+            uint4 q[3] = {next[0], next[1], next[2]};
+            if (gn < full)
+                load_words(pos, gn, next);
+            process_words<DT, kDisplace, kSplat>(q, g * G, G, P);
+            if constexpr (kDisplace)
+                store_words(pos, g, q);
+        } else {
+            process_tail<DT, kDisplace, kSplat>(pos, n, g * G, P);
+        }
+        g = gn;
+    }
+}
+
+// Persistent, TMA-staged variant of points_kernel.  The point buffer is cut
+// into tiles of kThreads 48-byte groups (12 KB at 256 threads); CTA b owns
+// tiles b, b + grid, b + 2 grid, ...  Thread 0 keeps kStages tiles in flight
+// with 1D bulk copies into shared memory, each completing on its own
+// mbarrier.  Every thread reads its group from shared memory (16-byte
+// accesses at a 48-byte stride: conflict-free), updates it in place and
+// splats; thread 0 then bulk-stores the tile back and refills the stage with
+// the CTA's next tile.  Global memory is touched only by whole-tile bulk
+// copies, so loads and stores are fully coalesced and many kilobytes per SM
+// are in flight.  Requires the buffer padded to whole groups (the library's
+// own allocations are).  Waits give up after kWaitCycles; the CTA then
+// raises *err and returns without storing.
+constexpr long long kWaitCycles = 1ll << 31;
+constexpr int kTmaStages = 4;
+
+template <int kThreads>
+constexpr uint32_t tma_smem_bytes()
+{
+    return kTmaStages * kThreads * 48u + kTmaStages * 8u;
+}
+
+template <int DT, bool kDisplace, bool kSplat, int kThreads>
+__global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__ pos, uint32_t n, PointParams P,
+                                                              uint32_t *__restrict__ err)
+{
+    constexpr int G = Group<DT>::kPoints;
+    constexpr uint32_t kTileBytes = kThreads * 48u;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kTmaStages * kTileBytes);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t total_groups = groups_of<DT>(n);
+    const uint32_t tiles = (total_groups + kThreads - 1) / kThreads;
+    if (blockIdx.x >= tiles)
+        return;
+    const uint32_t my_tiles = (tiles - 1 - blockIdx.x) / gridDim.x + 1;
+    char *gbase = static_cast<char *>(pos);
+    auto tile_of = [&](uint32_t k) { return blockIdx.x + k * gridDim.x; };
+    auto bytes_of = [&](uint32_t tile) { return min((uint32_t)kThreads, total_groups - tile * kThreads) * 48u; };
+
+    if (tid == 0) {
+        for (int st = 0; st < kTmaStages; ++st)
+            mbar_init(smem_addr(&bars[st]), 1);
+        mbar_init_fence();
+        for (uint32_t k = 0; k < my_tiles && k < (uint32_t)kTmaStages; ++k) {
+            const uint32_t tile = tile_of(k), bytes = bytes_of(tile), bar = smem_addr(&bars[k]);
+            mbar_arrive_expect_tx(bar, bytes);
+            bulk_load(smem_addr(smem + k * kTileBytes), gbase + (size_t)tile * kTileBytes, bytes, bar);
+        }
+    }
+    __syncthreads();
+
+    for (uint32_t k = 0; k < my_tiles; ++k) {
+        const uint32_t st = k % kTmaStages;
+        const uint32_t tile = tile_of(k);
+        unsigned char *stage = smem + st * kTileBytes;
+        const bool ok = mbar_wait_bounded(smem_addr(&bars[st]), (k / kTmaStages) & 1u, kWaitCycles);
+        const uint32_t g = tile * kThreads + tid;
+        if (ok && g < total_groups) {
+            uint4 q[3];
+            uint4 *mine = reinterpret_cast<uint4 *>(stage + tid * 48u);
+            q[0] = mine[0];
+            q[1] = mine[1];
+            q[2] = mine[2];
+            const uint32_t i0 = g * G;
+            process_words<DT, kDisplace, kSplat>(q, i0, min((uint32_t)G, n - i0), P);
+            if constexpr (kDisplace) {
+                mine[0] = q[0];
+                mine[1] = q[1];
+                mine[2] = q[2];
+            }
+        }
+        if constexpr (kDisplace)
+            fence_proxy_async_smem();
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicOr(err, 1u);
+                if constexpr (kDisplace)
+                    bulk_wait_all();
+            }
+            return;
+        }
+        if (tid == 0) {
+            if constexpr (kDisplace) {
+                bulk_store(gbase + (size_t)tile * kTileBytes, smem_addr(stage), bytes_of(tile));
+                bulk_commit();
+            }
+            const uint32_t kn = k + kTmaStages;
+            if (kn < my_tiles) {
+                if constexpr (kDisplace)
+                    bulk_wait_read_all();       // the store has left the stage
+                const uint32_t tn = tile_of(kn), bytes = bytes_of(tn), bar = smem_addr(&bars[st]);
+                mbar_arrive_expect_tx(bar, bytes);
+                bulk_load(smem_addr(stage), gbase + (size_t)tn * kTileBytes, bytes, bar);
+            }
+        }
+    }
+    if constexpr (kDisplace) {
+        if (tid == 0)
+            bulk_wait_all();
+    }
 }
 
 // Resolve + clear: four pixels per thread, grid-stride; the ragged tail
@@ -64,6 +191,67 @@ static cudaError_t launch_points_dt(void *pos, uint32_t n, const PointParams &P,
     return cudaGetLastError();
 }
 
+template <int DT, bool kD, bool kS, int kT>
+static cudaError_t launch_tma_one(void *pos, uint32_t n, const PointParams &P, uint32_t *err, int ctas_per_sm,
+                                  int sm_count, cudaStream_t s)
+{
+    constexpr uint32_t smem = tma_smem_bytes<kT>();
+    static unsigned long long configured = 0;    // one bit per device ordinal
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(points_tma_kernel<DT, kD, kS, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        configured |= bit;
+    }
+    const uint64_t tiles = (groups_of<DT>(n) + kT - 1) / kT;
+    const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sm_count * ctas_per_sm);
+    points_tma_kernel<DT, kD, kS, kT><<<grid, kT, smem, s>>>(pos, n, P, err);
+    return cudaGetLastError();
+}
+
+template <int DT, int kT>
+static cudaError_t launch_tma_dt(void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
+                                 uint32_t *err, int ctas_per_sm, int sm_count, cudaStream_t s)
+{
+    if (displace && splat)
+        return launch_tma_one<DT, true, true, kT>(pos, n, P, err, ctas_per_sm, sm_count, s);
+    if (displace)
+        return launch_tma_one<DT, true, false, kT>(pos, n, P, err, ctas_per_sm, sm_count, s);
+    return launch_tma_one<DT, false, true, kT>(pos, n, P, err, ctas_per_sm, sm_count, s);
+}
+
+template <int kT>
+static cudaError_t launch_tma_threads(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
+                                     bool splat, uint32_t *err, int ctas_per_sm, int sm_count, cudaStream_t s)
+{
+    switch (dtype) {
+    case kF32: return launch_tma_dt<kF32, kT>(pos, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
+    case kF16: return launch_tma_dt<kF16, kT>(pos, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
+    case kBF16: return launch_tma_dt<kBF16, kT>(pos, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_points_tma(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
+                              uint32_t *err, const LaunchShape &ls, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const int ctas = ls.ctas_per_sm > 0 ? ls.ctas_per_sm : 1;
+    switch (ls.threads) {
+    case 128: return launch_tma_threads<128>(dtype, pos, n, P, displace, splat, err, ctas, ls.sm_count, s);
+    case 256: return launch_tma_threads<256>(dtype, pos, n, P, displace, splat, err, ctas, ls.sm_count, s);
+    case 512: return launch_tma_threads<512>(dtype, pos, n, P, displace, splat, err, ctas, ls.sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_points(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
                           bool splat, const LaunchShape &ls, cudaStream_t s)
 {
@@ -81,9 +269,11 @@ cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *n
                            uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,
                            uint32_t background, const LaunchShape &ls, cudaStream_t s)
 {
+    // pure streaming: one quad per thread, 256 threads, whatever the point kernel's shape
+    (void)ls;
     const uint64_t quads = npx / 4;
-    int grid = grid_for(quads > 0 ? quads : 1, ls);
-    resolve_kernel<<<grid, ls.threads, 0, s>>>(keys, next_keys, rgba, colors, npx, color, background);
+    const int grid = (int)std::max<uint64_t>(1, (quads + 255) / 256);
+    resolve_kernel<<<grid, 256, 0, s>>>(keys, next_keys, rgba, colors, npx, color, background);
     return cudaGetLastError();
 }
 

@@ -29,48 +29,6 @@ struct Group<kBF16> {
 };
 
 template <int DT>
-__device__ __forceinline__ void load_group(const void *pos, uint32_t g, float *v)
-{
-    const uint4 *p4 = reinterpret_cast<const uint4 *>(pos) + 3ull * g;
-    uint4 q[3];
-    q[0] = __ldcs(p4 + 0);
-    q[1] = __ldcs(p4 + 1);
-    q[2] = __ldcs(p4 + 2);
-    if constexpr (DT == kF32) {
-        const uint32_t *w = reinterpret_cast<const uint32_t *>(q);
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-            v[k] = __uint_as_float(w[k]);
-    } else {
-        const uint16_t *h = reinterpret_cast<const uint16_t *>(q);
-#pragma unroll
-        for (int k = 0; k < 24; ++k)
-            v[k] = widen<DT>(h[k]);
-    }
-}
-
-template <int DT>
-__device__ __forceinline__ void store_group(void *pos, uint32_t g, const float *v)
-{
-    uint4 q[3];
-    if constexpr (DT == kF32) {
-        uint32_t *w = reinterpret_cast<uint32_t *>(q);
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-            w[k] = __float_as_uint(v[k]);
-    } else {
-        uint16_t *h = reinterpret_cast<uint16_t *>(q);
-#pragma unroll
-        for (int k = 0; k < 24; ++k)
-            h[k] = narrow<DT>(v[k]);
-    }
-    uint4 *p4 = reinterpret_cast<uint4 *>(pos) + 3ull * g;
-    __stcs(p4 + 0, q[0]);
-    __stcs(p4 + 1, q[1]);
-    __stcs(p4 + 2, q[2]);
-}
-
-template <int DT>
 __device__ __forceinline__ float load_coord(const void *pos, uint64_t k)
 {
     if constexpr (DT == kF32)
@@ -100,57 +58,100 @@ __device__ __forceinline__ float storage_round(float f)
         return widen<DT>(narrow<DT>(f));
 }
 
-// One thread's share of a point buffer: group g (G points, 48 bytes), or
-// the ragged tail of fewer than G points with scalar accesses.
+// The ragged tail: points i0 .. n-1 of the last, partial group, with scalar
+// accesses (the vector path would read past n).
 template <int DT, bool kDisplace, bool kSplat>
-__device__ __forceinline__ void process_group(void *__restrict__ pos, uint32_t n, uint32_t g,
-                                              const PointParams &P)
+__device__ __forceinline__ void process_tail(void *__restrict__ pos, uint32_t n, uint32_t i0, const PointParams &P)
 {
-    constexpr int G = Group<DT>::kPoints;
-    const uint32_t full = n / G;
-    const uint32_t i0 = g * G;
-    if (g < full) {
-        float v[3 * G];
-        load_group<DT>(pos, g, v);
+    for (uint32_t i = i0; i < n; ++i) {
+        float x = load_coord<DT>(pos, 3ull * i);
+        float y = load_coord<DT>(pos, 3ull * i + 1);
+        float z = load_coord<DT>(pos, 3ull * i + 2);
         if constexpr (kDisplace) {
-#pragma unroll
-            for (int j = 0; j < G; ++j) {
-                displace_point(v[3 * j], v[3 * j + 1], v[3 * j + 2], i0 + j, P);
-                v[3 * j + 0] = storage_round<DT>(v[3 * j + 0]);
-                v[3 * j + 1] = storage_round<DT>(v[3 * j + 1]);
-                v[3 * j + 2] = storage_round<DT>(v[3 * j + 2]);
-            }
-            store_group<DT>(pos, g, v);
+            displace_point(x, y, z, i, P);
+            x = storage_round<DT>(x);
+            y = storage_round<DT>(y);
+            z = storage_round<DT>(z);
+            store_coord<DT>(pos, 3ull * i, x);
+            store_coord<DT>(pos, 3ull * i + 1, y);
+            store_coord<DT>(pos, 3ull * i + 2, z);
         }
         if constexpr (kSplat) {
+            uint32_t px;
+            unsigned long long key;
+            if (project_key(x, y, z, P.id_base + i, P, px, key))
+                splat_key(P.keys, px, key);
+        }
+    }
+}
+
+// Group g (48 bytes) as three 16-byte streamed (evict-first) accesses.
+__device__ __forceinline__ void load_words(const void *pos, uint32_t g, uint4 (&q)[3])
+{
+    const uint4 *p4 = reinterpret_cast<const uint4 *>(pos) + 3ull * g;
+    q[0] = __ldcs(p4 + 0);
+    q[1] = __ldcs(p4 + 1);
+    q[2] = __ldcs(p4 + 2);
+}
+
+__device__ __forceinline__ void store_words(void *pos, uint32_t g, const uint4 (&q)[3])
+{
+    uint4 *p4 = reinterpret_cast<uint4 *>(pos) + 3ull * g;
+    __stcs(p4 + 0, q[0]);
+    __stcs(p4 + 1, q[1]);
+    __stcs(p4 + 2, q[2]);
+}
+
+// The points of one 48-byte group held as three 16-byte words (as loaded
+// from global or shared memory): displace in place and/or splat the first
+// `count` points (count == G except in the ragged last group).
+template <int DT>
+__device__ __forceinline__ float word_coord(const uint4 (&q)[3], int k)
+{
+    if constexpr (DT == kF32)
+        return __uint_as_float(reinterpret_cast<const uint32_t *>(q)[k]);
+    else
+        return widen<DT>(reinterpret_cast<const uint16_t *>(q)[k]);
+}
+
+template <int DT>
+__device__ __forceinline__ void set_word_coord(uint4 (&q)[3], int k, float f)
+{
+    if constexpr (DT == kF32)
+        reinterpret_cast<uint32_t *>(q)[k] = __float_as_uint(f);
+    else
+        reinterpret_cast<uint16_t *>(q)[k] = narrow<DT>(f);
+}
+
+template <int DT, bool kDisplace, bool kSplat>
+__device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32_t count, const PointParams &P)
+{
+    constexpr int G = Group<DT>::kPoints;
+    float v[3 * G];
 #pragma unroll
-            for (int j = 0; j < G; ++j) {
-                uint32_t px;
-                unsigned long long key;
-                if (project_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], P.id_base + i0 + j, P, px, key))
-                    splat_key(P.keys, px, key);
+    for (int k = 0; k < 3 * G; ++k)
+        v[k] = word_coord<DT>(q, k);
+    if constexpr (kDisplace) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {       // constant indices keep q and v in registers
+            if ((uint32_t)j < count) {
+                displace_point(v[3 * j], v[3 * j + 1], v[3 * j + 2], i0 + j, P);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    v[3 * j + c] = storage_round<DT>(v[3 * j + c]);
+                    set_word_coord<DT>(q, 3 * j + c, v[3 * j + c]);
+                }
             }
         }
-    } else {
-        for (uint32_t i = i0; i < n; ++i) {
-            float x = load_coord<DT>(pos, 3ull * i);
-            float y = load_coord<DT>(pos, 3ull * i + 1);
-            float z = load_coord<DT>(pos, 3ull * i + 2);
-            if constexpr (kDisplace) {
-                displace_point(x, y, z, i, P);
-                x = storage_round<DT>(x);
-                y = storage_round<DT>(y);
-                z = storage_round<DT>(z);
-                store_coord<DT>(pos, 3ull * i, x);
-                store_coord<DT>(pos, 3ull * i + 1, y);
-                store_coord<DT>(pos, 3ull * i + 2, z);
-            }
-            if constexpr (kSplat) {
-                uint32_t px;
-                unsigned long long key;
-                if (project_key(x, y, z, P.id_base + i, P, px, key))
-                    splat_key(P.keys, px, key);
-            }
+    }
+    if constexpr (kSplat) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            uint32_t px;
+            unsigned long long key;
+            if ((uint32_t)j < count &&
+                project_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], P.id_base + i0 + j, P, px, key))
+                splat_key(P.keys, px, key);
         }
     }
 }

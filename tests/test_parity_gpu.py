@@ -62,12 +62,35 @@ def test_gaussian_cluster_contention_bit_exact(dtype):
     _assert_same(gpu_run(*args), oracle_run(*args), dtype)
 
 
-@pytest.mark.parametrize("launch", [(32, 0), (128, 0), (1024, 0), (256, 1), (64, 3), (512, 8)])
+@pytest.mark.parametrize("launch", [(32, 0, 0), (128, 0, 0), (1024, 0, 0), (256, 1, 0), (64, 3, 0), (512, 8, 0),
+                                    (128, 3, 1), (256, 4, 1), (512, 1, 1), (256, 2, 1)])
 def test_launch_shape_does_not_change_results(launch):
     n = 70_001
     stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 22, components=4, sigma=0.05), "f32")
     args = (stored, "f32", 160, 90, 3, 1e-3, 3, orbit(10.0))
     _assert_same(gpu_run(*args, launch=launch), oracle_run(*args), f"launch {launch}")
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+@pytest.mark.parametrize("launch", [(256, 4, 0), (256, 2, 1), (128, 8, 1)])
+def test_launch_shapes_16bit(launch, dtype):
+    n = 33_333
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 27, components=4, sigma=0.05), dtype)
+    args = (stored, dtype, 96, 72, 3, 1e-3, 3, orbit(7.0))
+    _assert_same(gpu_run(*args, launch=launch), oracle_run(*args), f"{dtype} launch {launch}")
+
+
+def test_launch_validation():
+    from paper_2504_20937_b300.api import Context, MmrError
+    with Context(16, 16) as ctx:
+        with pytest.raises(MmrError, match="INVALID"):
+            ctx.set_launch(64, 2, 1)         # TMA needs 128/256/512 threads
+        with pytest.raises(MmrError, match="INVALID"):
+            ctx.set_launch(256, 0, 1)        # and a persistent grid
+        with pytest.raises(MmrError, match="INVALID"):
+            ctx.set_launch(256, 0, 7)
+        ctx.set_launch(256, 2, 1)
+        ctx.check_device()
 
 
 @pytest.mark.parametrize("mode", ["split", "roundtrip", "roundtrip_pageable"])
