@@ -262,6 +262,74 @@ MMR_API mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t *
 MMR_API mmr_status mmr_batch_frames(const mmr_batch *b, uint32_t *frames);
 MMR_API mmr_status mmr_batch_device_bytes(const mmr_batch *b, uint64_t *bytes);
 
+/* ---- serving: many viewers of one shared cloud -----------------------------
+ * A serving engine holds one shared point cloud and up to any number of
+ * viewers, each with a private cloud, a camera and a framebuffer.  One call
+ * of mmr_serve_tick renders one frame for every active viewer:
+ *  - the shared cloud is displaced once (Philox step = tick index) and every
+ *    shared point is splatted into every active viewer's buffer in the same
+ *    pass, so its positions are read once per tick;
+ *  - each viewer's private cloud is displaced (step = that viewer's frame
+ *    index) and splatted into its own buffer, all viewers in one launch;
+ *  - one resolve launch writes every viewer's RGBA8 frame: shared points in
+ *    the shared colour, private points in the viewer's colour.
+ * Point ids in the keys: shared point i -> i, private point j -> shared_n + j.
+ * Viewers join and leave between ticks (continuous batching); a join whose
+ * buffers would exceed the budget is refused with MMR_ERR_BUDGET and can be
+ * retried after others leave.  Frame k of a viewer that joined before tick t0
+ * is rendered at tick t0 + k and depends only on (t0 + k, k): it is the same
+ * whether the viewer is served alone or with others. */
+typedef struct mmr_serve mmr_serve;
+
+/* Engine with a shared cloud of shared_n points (1..2^31-1) stored as dtype,
+ * displaced with Philox key `seed`, counter word 2 `cloud`, and amplitude.
+ * budget_bytes caps the device memory of the shared cloud and all viewers
+ * (0 = no cap). */
+MMR_API mmr_status mmr_serve_create(uint64_t shared_n, int dtype, uint64_t seed, uint32_t cloud, float amplitude,
+                                    uint64_t budget_bytes, mmr_serve **out);
+MMR_API mmr_status mmr_serve_destroy(mmr_serve *s);
+MMR_API const char *mmr_serve_last_error(const mmr_serve *s);
+
+/* Device pointer of the shared positions (write them before the first tick). */
+MMR_API mmr_status mmr_serve_shared_points(mmr_serve *s, void **dev_ptr);
+MMR_API mmr_status mmr_serve_set_shared_color(mmr_serve *s, uint32_t color);
+
+/* Admit a viewer: private cloud of private_n points (zero-filled; write it
+ * through mmr_serve_viewer_points before its first tick), a width x height
+ * framebuffer, its own Philox key/cloud word/amplitude and colours.  Returns
+ * the viewer id in *viewer.  MMR_ERR_BUDGET when it does not fit (nothing is
+ * allocated then).  shared_n + private_n must stay below 2^32. */
+MMR_API mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int height, uint64_t seed,
+                                        uint32_t cloud, float amplitude, uint32_t color, uint32_t background,
+                                        int *viewer);
+MMR_API mmr_status mmr_serve_viewer_points(mmr_serve *s, int viewer, void **dev_ptr);
+
+/* Camera of a viewer for the next tick (as mmr_set_camera, viewer aspect). */
+MMR_API mmr_status mmr_serve_set_camera(mmr_serve *s, int viewer, const double eye[3], const double target[3],
+                                        const double up[3], double fovy_deg, double znear, double zfar);
+
+/* Release a viewer's memory after the last enqueued tick has finished. */
+MMR_API mmr_status mmr_serve_remove_viewer(mmr_serve *s, int viewer);
+
+/* One tick on `stream` (every active viewer needs a camera).  The
+ * _roundtrip form first sends the shared positions device -> pinned host ->
+ * device (the paper's RAM-based comparison); results are identical. */
+MMR_API mmr_status mmr_serve_tick(mmr_serve *s, void *stream);
+MMR_API mmr_status mmr_serve_tick_roundtrip(mmr_serve *s, void *stream);
+
+/* Latest frame of a viewer (device pointers) and how many frames it has had. */
+MMR_API mmr_status mmr_serve_frame_ptr(mmr_serve *s, int viewer, const uint32_t **rgba, const uint64_t **depth_id,
+                                       uint32_t *frame_index);
+
+/* Ticks so far, active viewers, device bytes held (any pointer may be NULL). */
+MMR_API mmr_status mmr_serve_status(const mmr_serve *s, uint32_t *tick, int *active_viewers,
+                                    uint64_t *device_bytes);
+
+/* CUDA-event timing of each tick's kernels; mmr_serve_last_tick_ms waits for
+ * the latest tick and returns its device time. */
+MMR_API mmr_status mmr_serve_set_timing(mmr_serve *s, int enable);
+MMR_API mmr_status mmr_serve_last_tick_ms(mmr_serve *s, float *ms);
+
 /* ---- rendering without allocation ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot call cudaMalloc.  Examples: a simulation embedded in a host

@@ -78,6 +78,23 @@ SIGNATURES.update({
     "mmr_batch_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
 })
 
+SIGNATURES.update({
+    "mmr_serve_create": (_i, [_u64, _i, _u64, _u32, _f, _u64, C.POINTER(_vp)]),
+    "mmr_serve_destroy": (_i, [_vp]),
+    "mmr_serve_last_error": (C.c_char_p, [_vp]),
+    "mmr_serve_shared_points": (_i, [_vp, C.POINTER(_vp)]),
+    "mmr_serve_set_shared_color": (_i, [_vp, _u32]),
+    "mmr_serve_add_viewer": (_i, [_vp, _u64, _i, _i, _u64, _u32, _f, _u32, _u32, C.POINTER(_i)]),
+    "mmr_serve_viewer_points": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "mmr_serve_set_camera": (_i, [_vp, _i, _d3, _d3, _d3, _d, _d, _d]),
+    "mmr_serve_remove_viewer": (_i, [_vp, _i]),
+    "mmr_serve_tick": (_i, [_vp, _vp]),
+    "mmr_serve_tick_roundtrip": (_i, [_vp, _vp]),
+    "mmr_serve_frame_ptr": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_u32)]),
+    "mmr_serve_status": (_i, [_vp, C.POINTER(_u32), C.POINTER(_i), C.POINTER(_u64)]),
+    "mmr_serve_set_timing": (_i, [_vp, _i]),
+    "mmr_serve_last_tick_ms": (_i, [_vp, C.POINTER(_f)]),
+})
 SIGNATURES["mmr_render_static"] = (_i, [_vp, _u64, _i, _f16, _f, _f, _i, _i, _u32, _u32, _vp, _vp])
 STATIC_MAX_PIXELS = 4194304
 
@@ -105,10 +122,15 @@ def load() -> C.CDLL:
     return _lib
 
 
-def check(status: int, ctx=None, batch=False) -> None:
+def check(status: int, ctx=None, batch=False, serve=False) -> None:
     if status != MMR_OK:
         lib = load()
-        msg = lib.mmr_batch_last_error(ctx) if batch else lib.mmr_last_error(ctx)
+        if serve:
+            msg = lib.mmr_serve_last_error(ctx)
+        elif batch:
+            msg = lib.mmr_batch_last_error(ctx)
+        else:
+            msg = lib.mmr_last_error(ctx)
         raise MmrError(status, msg.decode() if msg else "")
 
 

@@ -260,4 +260,102 @@ class Batch:
         return b.value
 
 
-__all__ = ["Batch", "Context", "MmrError", "device_view"]
+class Server:
+    """Serving engine (mmr_serve_*): a shared cloud plus per-viewer private
+    clouds, one frame per active viewer per tick."""
+
+    def __init__(self, shared_n: int, dtype: str = "f32", seed: int = 0, cloud: int = 0, amplitude: float = 5e-4,
+                 budget_bytes: int = 0):
+        lib = _lib.load()
+        h = C.c_void_p()
+        check(lib.mmr_serve_create(shared_n, DTYPE_CODE[dtype], seed, cloud, amplitude, budget_bytes, C.byref(h)),
+              None, serve=True)
+        self._lib, self._h = lib, h
+        self.shared_n, self.dtype = shared_n, dtype
+        self.viewers = {}
+
+    def close(self):
+        if self._h:
+            self._lib.mmr_serve_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status):
+        check(status, self._h, serve=True)
+
+    def shared_points(self) -> torch.Tensor:
+        p = C.c_void_p()
+        self._check(self._lib.mmr_serve_shared_points(self._h, C.byref(p)))
+        return device_view(p.value, (self.shared_n, 3), _TORCH_VIEW[self.dtype][1])
+
+    def set_shared_color(self, color: int):
+        self._check(self._lib.mmr_serve_set_shared_color(self._h, color))
+
+    def add_viewer(self, private_n: int, width: int, height: int, seed: int = 0, cloud: int = 1,
+                   amplitude: float = 5e-4, color: int = 0xFFFFFFFF, background: int = 0) -> int:
+        """Viewer id; raises MmrError (MMR_ERR_BUDGET) when it does not fit."""
+        v = C.c_int()
+        self._check(self._lib.mmr_serve_add_viewer(self._h, private_n, width, height, seed, cloud, amplitude,
+                                                   color, background, C.byref(v)))
+        self.viewers[v.value] = (private_n, width, height)
+        return v.value
+
+    def try_add_viewer(self, *args, **kw):
+        """As add_viewer, but None instead of an exception when over budget."""
+        try:
+            return self.add_viewer(*args, **kw)
+        except MmrError as e:
+            if e.status == -3:
+                return None
+            raise
+
+    def viewer_points(self, v: int) -> torch.Tensor:
+        p = C.c_void_p()
+        self._check(self._lib.mmr_serve_viewer_points(self._h, v, C.byref(p)))
+        return device_view(p.value, (self.viewers[v][0], 3), _TORCH_VIEW[self.dtype][1])
+
+    def set_camera(self, v: int, eye, target, up, fovy_deg, znear, zfar):
+        d3 = C.c_double * 3
+        self._check(self._lib.mmr_serve_set_camera(self._h, v, d3(*eye), d3(*target), d3(*up), fovy_deg, znear, zfar))
+
+    def remove_viewer(self, v: int):
+        self._check(self._lib.mmr_serve_remove_viewer(self._h, v))
+        self.viewers.pop(v, None)
+
+    def tick(self, stream=None, roundtrip: bool = False):
+        fn = self._lib.mmr_serve_tick_roundtrip if roundtrip else self._lib.mmr_serve_tick
+        self._check(fn(self._h, stream_handle(stream)))
+
+    def frame(self, v: int):
+        """(rgba int32[H,W] view, keys int64[H,W] view, frames rendered so far)."""
+        r, k, f = C.c_void_p(), C.c_void_p(), C.c_uint32()
+        self._check(self._lib.mmr_serve_frame_ptr(self._h, v, C.byref(r), C.byref(k), C.byref(f)))
+        _, W, H = self.viewers[v]
+        return device_view(r.value, (H, W), "<i4"), device_view(k.value, (H, W), "<i8"), f.value
+
+    def status(self):
+        t, a, b = C.c_uint32(), C.c_int(), C.c_uint64()
+        self._check(self._lib.mmr_serve_status(self._h, C.byref(t), C.byref(a), C.byref(b)))
+        return {"tick": t.value, "active": a.value, "device_bytes": b.value}
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._lib.mmr_serve_set_timing(self._h, int(enable)))
+
+    def last_tick_ms(self) -> float:
+        ms = C.c_float()
+        self._check(self._lib.mmr_serve_last_tick_ms(self._h, C.byref(ms)))
+        return ms.value
+
+
+__all__ = ["Batch", "Context", "MmrError", "Server", "device_view"]

@@ -1,0 +1,153 @@
+"""Continuous-batching request loop over the serving engine (mmr_serve_*).
+
+Viewers arrive over time (a trace from inputs.serving_trace), each asking
+for a run of frames of its own resolution with its own private cloud.  The
+loop admits arrived viewers while there is a free slot and the engine's
+device-memory budget allows (a refused viewer waits in FIFO order), runs one
+engine tick per iteration (one frame for every active viewer, all of them
+batched into the same kernels), and retires viewers when their last frame is
+done, which frees memory for the queue.  A frame's latency is the time from
+its request (the viewer's arrival for its first frame, the completion of its
+previous frame otherwise) to the completion of the tick that rendered it.
+
+The scheduling decisions and the bookkeeping live here; all device work is
+in the library.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import inputs
+from .api import Server
+
+CENTRE = (0.5, 0.5, 0.5)
+UP = (0.0, 1.0, 0.0)
+
+
+@dataclass
+class ServeConfig:
+    shared_n: int = 1 << 24
+    shared_seed: int = 5
+    dtype: str = "f32"
+    amplitude: float = 5e-4
+    budget_bytes: int = 40 << 30
+    max_viewers: int = 64
+    shared_color: int = 0xFFFFFFFF
+    deg_per_frame: float = 0.36
+    fovy_deg: float = 60.0
+    znear: float = 0.1
+    zfar: float = 100.0
+
+
+@dataclass
+class ServeStats:
+    frames: int = 0
+    ticks: int = 0
+    wall_s: float = 0.0
+    tick_ms: list = field(default_factory=list)
+    latencies_ms: list = field(default_factory=list)
+    steady_latencies_ms: list = field(default_factory=list)   # frames after a viewer's first
+    active_per_tick: list = field(default_factory=list)
+    points_rendered: int = 0
+    max_active: int = 0
+    refused_for_budget: int = 0
+    queue_wait_ms: list = field(default_factory=list)
+
+    def summary(self) -> dict:
+        lat = np.asarray(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        steady = np.asarray(self.steady_latencies_ms) if self.steady_latencies_ms else np.zeros(1)
+        return {"frames": self.frames, "ticks": self.ticks, "wall_s": self.wall_s,
+                "frames_per_s": self.frames / self.wall_s if self.wall_s else 0.0,
+                "points_per_s": self.points_rendered / self.wall_s if self.wall_s else 0.0,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "p50_ms_after_first": float(np.percentile(steady, 50)),
+                "p99_ms_after_first": float(np.percentile(steady, 99)),
+                "mean_active_viewers": float(np.mean(self.active_per_tick)) if self.active_per_tick else 0.0,
+                "min_active_viewers": int(min(self.active_per_tick)) if self.active_per_tick else 0,
+                "mean_tick_ms": float(np.mean(self.tick_ms)) if self.tick_ms else 0.0,
+                "max_active_viewers": self.max_active, "refused_for_budget": self.refused_for_budget,
+                "p99_queue_wait_ms": float(np.percentile(self.queue_wait_ms, 99)) if self.queue_wait_ms else 0.0}
+
+
+def viewer_eye(req: inputs.ViewerRequest, frame: int, cfg: ServeConfig):
+    return inputs.orbit_eye(frame, cfg.deg_per_frame, 2.0, CENTRE, 0.0, req.start_deg)
+
+
+def private_cloud(req: inputs.ViewerRequest, dtype: str) -> np.ndarray:
+    return inputs.encode(inputs.uniform_cloud(req.private_n, req.init_seed), dtype)
+
+
+def _to_torch(stored: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(stored if stored.dtype == np.float32 else stored.view(np.int16))
+
+
+def run_trace(trace, cfg: ServeConfig, roundtrip: bool = False, clouds=None, shared=None) -> ServeStats:
+    """Serve every request of `trace`; returns the statistics.
+
+    clouds: optional {viewer: stored private cloud} (generated if missing);
+    shared: optional stored shared cloud (generated if missing).
+    """
+    if shared is None:
+        shared = inputs.encode(inputs.uniform_cloud(cfg.shared_n, cfg.shared_seed), cfg.dtype)
+    if clouds is None:
+        clouds = {r.viewer: private_cloud(r, cfg.dtype) for r in trace}
+    host_clouds = {v: _to_torch(c).pin_memory() for v, c in clouds.items()}
+    stats = ServeStats()
+    stream = torch.cuda.current_stream()
+    with Server(cfg.shared_n, cfg.dtype, cfg.shared_seed, 0, cfg.amplitude, cfg.budget_bytes) as srv:
+        srv.shared_points().copy_(_to_torch(shared))
+        srv.set_shared_color(cfg.shared_color)
+        srv.set_timing(True)
+        torch.cuda.synchronize()
+        pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
+        waiting = collections.deque()
+        active = {}                     # engine viewer id -> [request, frames done, request time]
+        t0 = time.perf_counter()
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival_s <= now:
+                waiting.append(pending.popleft())
+            while waiting and len(active) < cfg.max_viewers:
+                req = waiting[0]
+                vid = srv.try_add_viewer(req.private_n, req.W, req.H, seed=req.init_seed, cloud=1 + req.viewer,
+                                         amplitude=cfg.amplitude, color=0xFF000000 | (req.viewer & 0xFFFFFF))
+                if vid is None:
+                    stats.refused_for_budget += 1
+                    break
+                waiting.popleft()
+                srv.viewer_points(vid).copy_(host_clouds[req.viewer], non_blocking=True)
+                stats.queue_wait_ms.append(1e3 * max(0.0, (time.perf_counter() - t0) - req.arrival_s))
+                active[vid] = [req, 0, req.arrival_s]
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival_s - now, 0.001)))
+                continue
+            stats.max_active = max(stats.max_active, len(active))
+            stats.active_per_tick.append(len(active))
+            for vid, (req, k, _) in active.items():
+                srv.set_camera(vid, viewer_eye(req, k, cfg), CENTRE, UP, cfg.fovy_deg, cfg.znear, cfg.zfar)
+            srv.tick(stream, roundtrip=roundtrip)
+            stats.tick_ms.append(srv.last_tick_ms())      # waits for the tick
+            done = time.perf_counter() - t0
+            stats.ticks += 1
+            finished = []
+            for vid, st in active.items():
+                req, k, req_time = st
+                stats.latencies_ms.append(1e3 * (done - req_time))
+                if k > 0:
+                    stats.steady_latencies_ms.append(1e3 * (done - req_time))
+                stats.frames += 1
+                stats.points_rendered += cfg.shared_n + req.private_n
+                st[1], st[2] = k + 1, done
+                if st[1] >= req.frames:
+                    finished.append(vid)
+            for vid in finished:
+                srv.remove_viewer(vid)
+                del active[vid]
+        stats.wall_s = time.perf_counter() - t0
+    return stats

@@ -1,0 +1,174 @@
+"""Serving engine: frames against the oracle, the same frame alone and in a
+mix of viewers (bit for bit), budget admission, the round-trip baseline,
+and the continuous-batching request loop."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_20937_b300 import inputs
+from paper_2504_20937_b300.api import MmrError, Server
+from paper_2504_20937_b300.serve import ServeConfig, run_trace
+
+pytestmark = pytest.mark.gpu
+
+CEN = (0.5, 0.5, 0.5)
+UP = (0.0, 1.0, 0.0)
+SHARED_N, SHARED_SEED, AMP = 20_001, 77, np.float32(1e-3)
+SHARED_COLOR = 0xFFEEDDCC
+
+# (private n, W, H, join tick, frames)
+VIEWERS = [(1, 64, 48, 0, 6), (999, 37, 23, 2, 2), (5000, 128, 96, 3, 3), (12_345, 80, 60, 1, 5)]
+
+
+def _eye(v, k):
+    return inputs.orbit_eye(k, 5.0, 2.0 + 0.1 * v, CEN, 0.1 * v, 40.0 * v)
+
+
+def _private(v, n):
+    return inputs.encode(inputs.uniform_cloud(n, 900 + v), "f32")
+
+
+def _shared():
+    return inputs.encode(inputs.uniform_cloud(SHARED_N, 901), "f32")
+
+
+def _viewer_args(v, n, W, H):
+    return dict(private_n=n, width=W, height=H, seed=3000 + v, cloud=1 + v, amplitude=float(AMP),
+                color=0xFF000000 | v, background=0x10 + v)
+
+
+def _run_mix(viewers, record, roundtrip=False):
+    """Drive the engine through `viewers`; returns {(v, k): (keys, rgba)} for
+    the requested (viewer, frame) pairs, plus the final shared positions."""
+    out = {}
+    with Server(SHARED_N, "f32", SHARED_SEED, 0, float(AMP)) as srv:
+        srv.shared_points().copy_(torch.from_numpy(_shared()))
+        srv.set_shared_color(SHARED_COLOR)
+        ids, done = {}, {}
+        last_tick = max(j + f for (_, _, _, j, f) in viewers)
+        for tick in range(last_tick):
+            for v, (n, W, H, join, frames) in enumerate(viewers):
+                if join == tick:
+                    ids[v] = srv.add_viewer(**_viewer_args(v, n, W, H))
+                    srv.viewer_points(ids[v]).copy_(torch.from_numpy(_private(v, n)))
+                    done[v] = 0
+            for v, vid in ids.items():
+                srv.set_camera(vid, _eye(v, done[v]), CEN, UP, 60.0, 0.1, 100.0)
+            srv.tick(roundtrip=roundtrip)
+            torch.cuda.synchronize()
+            for v in list(ids):
+                done[v] += 1
+                if (v, done[v] - 1) in record:
+                    rgba, keys, f = srv.frame(ids[v])
+                    assert f == done[v]
+                    out[(v, done[v] - 1)] = (keys.cpu().numpy().reshape(-1).view(np.uint64),
+                                             rgba.cpu().numpy().reshape(-1).view(np.uint32))
+                if done[v] == viewers[v][4]:
+                    srv.remove_viewer(ids.pop(v))
+        shared = srv.shared_points().cpu().numpy()
+    return out, shared
+
+
+def _oracle_frame(v, k, join):
+    n, W, H = VIEWERS[v][0], VIEWERS[v][1], VIEWERS[v][2]
+    shared = _shared()
+    for t in range(join + k + 1):
+        oracle.displace_f32(shared, SHARED_SEED, 0, t, AMP)
+    priv = _private(v, n)
+    for s in range(k + 1):
+        oracle.displace_f32(priv, 3000 + v, 1 + v, s, AMP)
+    both = np.concatenate([shared, priv])
+    colors = np.concatenate([np.full(SHARED_N, SHARED_COLOR, np.uint32), np.full(n, 0xFF000000 | v, np.uint32)])
+    M = oracle.camera_f32(_eye(v, k), CEN, UP, 60.0, W / H, 0.1, 100.0)
+    return oracle.render(both, "f32", M, W, H, np.float32(0.1), np.float32(100.0), colors, 0, 0x10 + v)
+
+
+def test_serve_frames_match_oracle():
+    record = {(0, 0), (0, 5), (1, 1), (2, 0), (2, 2), (3, 4)}
+    got, shared = _run_mix(VIEWERS, record)
+    for (v, k) in sorted(record):
+        keys, rgba = _oracle_frame(v, k, VIEWERS[v][3])
+        assert np.array_equal(got[(v, k)][0], keys), f"keys of viewer {v} frame {k}"
+        assert np.array_equal(got[(v, k)][1], rgba), f"rgba of viewer {v} frame {k}"
+    want = _shared()
+    for t in range(max(j + f for (_, _, _, j, f) in VIEWERS)):
+        oracle.displace_f32(want, SHARED_SEED, 0, t, AMP)
+    assert np.array_equal(shared, want)
+
+
+def test_serve_alone_equals_mix():
+    """Each viewer's frames are identical when it is the only viewer (same
+    join tick, so the shared cloud is at the same step) and when it is
+    served together with the others; tolerance 0."""
+    record = {(v, k) for v, vw in enumerate(VIEWERS) for k in range(vw[4])}
+    mix, _ = _run_mix(VIEWERS, record)
+    for v, vw in enumerate(VIEWERS):
+        alone, _ = _run_alone(v)
+        for k in range(vw[4]):
+            assert np.array_equal(mix[(v, k)][0], alone[(v, k)][0]), f"keys viewer {v} frame {k}"
+            assert np.array_equal(mix[(v, k)][1], alone[(v, k)][1]), f"rgba viewer {v} frame {k}"
+
+
+def _run_alone(v):
+    n, W, H, join, frames = VIEWERS[v]
+    out = {}
+    with Server(SHARED_N, "f32", SHARED_SEED, 0, float(AMP)) as srv:
+        srv.shared_points().copy_(torch.from_numpy(_shared()))
+        srv.set_shared_color(SHARED_COLOR)
+        for _ in range(join):
+            srv.tick()                          # no viewers: only the shared cloud moves
+        vid = srv.add_viewer(**_viewer_args(v, n, W, H))
+        srv.viewer_points(vid).copy_(torch.from_numpy(_private(v, n)))
+        for k in range(frames):
+            srv.set_camera(vid, _eye(v, k), CEN, UP, 60.0, 0.1, 100.0)
+            srv.tick()
+            torch.cuda.synchronize()
+            rgba, keys, _ = srv.frame(vid)
+            out[(v, k)] = (keys.cpu().numpy().reshape(-1).view(np.uint64),
+                           rgba.cpu().numpy().reshape(-1).view(np.uint32))
+    return out, None
+
+
+def test_serve_roundtrip_gives_same_frames():
+    record = {(v, VIEWERS[v][4] - 1) for v in range(len(VIEWERS))}
+    a, sa = _run_mix(VIEWERS, record)
+    b, sb = _run_mix(VIEWERS, record, roundtrip=True)
+    assert np.array_equal(sa, sb)
+    for key in record:
+        assert np.array_equal(a[key][0], b[key][0]) and np.array_equal(a[key][1], b[key][1])
+
+
+def test_serve_budget_admission_and_release():
+    shared_bytes = (SHARED_N * 12 + 47) // 48 * 48
+    viewer_bytes = (1000 * 12 + 47) // 48 * 48 + 64 * 64 * 20
+    with Server(SHARED_N, "f32", 1, 0, 1e-3, budget_bytes=shared_bytes + viewer_bytes + 100) as srv:
+        a = srv.add_viewer(1000, 64, 64)
+        assert srv.try_add_viewer(1000, 64, 64) is None          # refused, nothing allocated
+        with pytest.raises(MmrError, match="BUDGET"):
+            srv.add_viewer(1000, 64, 64)
+        with pytest.raises(MmrError, match="STATE"):
+            srv.tick()                                            # viewer a has no camera yet
+        srv.set_camera(a, (0.5, 0.5, 2.5), CEN, UP, 60.0, 0.1, 100.0)
+        srv.tick()
+        srv.remove_viewer(a)
+        b = srv.add_viewer(1000, 64, 64)                          # fits again
+        assert srv.status()["active"] == 1 and b is not None
+        with pytest.raises(MmrError, match="INVALID"):
+            srv.add_viewer(0, 64, 64)
+
+
+def test_serve_request_loop_small_trace():
+    trace = inputs.serving_trace(requests=200, seed=11, rate_hz=5000.0, frames_per_viewer=5,
+                                 private_lo=1e3, private_hi=2e4, resolutions=((64, 48), (160, 90), (320, 240)))
+    cfg = ServeConfig(shared_n=50_000, max_viewers=8)
+    stats = run_trace(trace, cfg)
+    s = stats.summary()
+    assert s["frames"] == sum(r.frames for r in trace)
+    assert 0 < s["p50_ms"] <= s["p99_ms"]
+    assert 1 <= s["max_active_viewers"] <= 8
+    # a budget for the shared cloud plus two of the largest viewers forces queueing on memory
+    tight = ServeConfig(shared_n=50_000, max_viewers=8,
+                        budget_bytes=(50_000 * 12 + 47) // 48 * 48 + 2 * (20_000 * 12 + 48 + 320 * 240 * 20))
+    s2 = run_trace(trace, tight).summary()
+    assert s2["frames"] == s["frames"] and s2["refused_for_budget"] > 0
