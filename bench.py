@@ -177,6 +177,27 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+# ----------------------------------------------------------- multi-rank glue
+
+def reduce_max(value: float) -> float:
+    """Max of `value` over all ranks (the value itself in a single process).
+    Each rank runs an independent replica of the workload, so this timing
+    reduction is the only collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 # --------------------------------------------------------------------- ours
 
 def run_ours(args, rank, world, local):
@@ -236,14 +257,11 @@ def run_ours(args, rank, world, local):
         step_ms, point_ms, resolve_ms = timed_frames(ctx, sc, args.steps, args.warmup, True)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    total_ms = sum(step_ms)
+    total_ms = reduce_max(sum(step_ms))
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
     n = sc.n
-    pts_per_s = world * args.steps * n / (total_ms / 1e3)
+    pts_per_s = job_rate(args.steps * n, world, total_ms)
     hbm_gbs, peak_kind = measured_peaks()
     bytes_point = 24 * n
     bytes_frame = bytes_point + 20 * sc.W * sc.H
@@ -261,7 +279,7 @@ def run_ours(args, rank, world, local):
                    "l2": f"flushed before every timed frame ({FLUSH_BYTES >> 20} MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "launch": args.launch or "library default (grid-stride, 128 threads, one thread per 48-byte group)"},
-        "frames_per_s": world * args.steps / (total_ms / 1e3),
+        "frames_per_s": job_rate(args.steps, world, total_ms),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "hbm_gbs_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9,
         "kernels_ms": {"points_fused": mean_point_ms, "resolve": statistics.mean(resolve_ms)},

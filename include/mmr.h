@@ -184,6 +184,13 @@ MMR_API mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *reso
  * last check.  A timed-out frame is incomplete; the context stays usable. */
 MMR_API mmr_status mmr_check_device(mmr_ctx *ctx);
 
+/* Failure-path self-test: one CTA waits on a barrier that nothing ever
+ * completes, gives up after max_cycles SM clock cycles (1..2^32) and raises
+ * the context's device error flag, exactly as a point kernel whose bulk copy
+ * never arrived would.  mmr_check_device then reports MMR_ERR_TIMEOUT and the
+ * context stays usable.  No fault and no unbounded wait is involved. */
+MMR_API mmr_status mmr_selftest_bounded_wait(mmr_ctx *ctx, long long max_cycles, void *stream);
+
 /* Device bytes this context holds right now. */
 MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
 

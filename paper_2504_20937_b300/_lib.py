@@ -50,6 +50,7 @@ SIGNATURES = {
     "mmr_get_step": (_i, [_vp, C.POINTER(_u32)]),
     "mmr_set_timing": (_i, [_vp, _i]),
     "mmr_check_device": (_i, [_vp]),
+    "mmr_selftest_bounded_wait": (_i, [_vp, C.c_longlong, _vp]),
     "mmr_last_kernel_ms": (_i, [_vp, C.POINTER(_f), C.POINTER(_f)]),
     "mmr_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
 }

@@ -146,6 +146,10 @@ class Context:
         """Raise MmrError(MMR_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
         self._check(self._lib.mmr_check_device(self._h))
 
+    def selftest_bounded_wait(self, max_cycles: int = 1_000_000, stream=None):
+        """Run the bounded-wait self-test kernel (see include/mmr.h)."""
+        self._check(self._lib.mmr_selftest_bounded_wait(self._h, max_cycles, stream_handle(stream)))
+
     def set_timing(self, enable: bool = True):
         self._check(self._lib.mmr_set_timing(self._h, int(enable)))
 

@@ -284,7 +284,7 @@ mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx *
     c->W = width;
     c->H = height;
     c->budget = budget_bytes;
-    c->launch.threads = 128;          // fastest measured shape (grid-stride, one thread per group)
+    c->launch.threads = 64;           // fastest measured shape (grid-stride, one thread per group)
     c->launch.ctas_per_sm = 0;
     c->launch.kernel = MMR_KERNEL_GRID;
     cudaError_t e = cudaGetDevice(&c->device);
@@ -646,6 +646,16 @@ mmr_status mmr_check_device(mmr_ctx *ctx)
         cudaMemset(ctx->d_err, 0, 4);
         return fail(ctx, MMR_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy (error word %u)", word);
     }
+    return MMR_OK;
+}
+
+mmr_status mmr_selftest_bounded_wait(mmr_ctx *ctx, long long max_cycles, void *stream)
+{
+    if (!ctx || max_cycles < 1 || max_cycles > (1ll << 32))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_selftest_bounded_wait: max_cycles outside 1..2^32");
+    cudaError_t e = mmr::launch_bounded_wait_selftest(max_cycles, ctx->d_err, (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_selftest_bounded_wait");
     return MMR_OK;
 }
 

@@ -24,6 +24,10 @@ cudaError_t launch_points(int dtype, void *pos, uint32_t n, const PointParams &P
 cudaError_t launch_points_tma(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
                               uint32_t *err, const LaunchShape &ls, cudaStream_t s);
 
+// One CTA that waits on an mbarrier nothing arrives on, for max_cycles, then
+// sets *err like a point kernel whose bulk copy never completed.
+cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cudaStream_t s);
+
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys,
                            uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,
                            uint32_t background, const LaunchShape &ls, cudaStream_t s);

@@ -146,6 +146,28 @@ __global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__
     }
 }
 
+// Self-test of the bounded wait used by the TMA kernel: wait on an mbarrier
+// that nothing ever arrives on, give up after max_cycles and report it the
+// same way the point kernel does.
+__global__ void bounded_wait_selftest_kernel(long long max_cycles, uint32_t *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(smem_addr(&bar), 0, max_cycles);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0)
+        atomicOr(err, 1u);
+}
+
+cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cudaStream_t s)
+{
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(max_cycles, err);
+    return cudaGetLastError();
+}
+
 // Resolve + clear: four pixels per thread, grid-stride; the ragged tail
 // (npx not a multiple of 4) goes to the first threads.
 __global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
