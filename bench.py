@@ -326,6 +326,7 @@ def run_ours(args, rank, world, local):
                               " and synchronised every frame"}
         ctx.close()
         out["c3_64Mpts_gmm16_3840x2160"] = run_c3(make_ctx, timed_frames, hbm_gbs)
+        out["features_c2"] = run_features(sc, stored, hbm_gbs)
         out["batched_256_clouds"] = run_batched(hbm_gbs)
         out["served"] = run_served()
     else:
@@ -357,6 +358,55 @@ def run_c3(make_ctx, timed_frames, hbm_gbs, frames=20):
                       "points_kernel_gbs": bpp * sc.n / (pk / 1e3) / 1e9,
                       "points_kernel_frac": bpp * sc.n / (pk / 1e3) / 1e9 / hbm_gbs}
         del data
+    return res
+
+
+def run_features(sc, stored, hbm_gbs, frames=50):
+    """The same 2^22-point 1920x1080 orbit with the paper's other usage
+    patterns: ping-pong buffers (step out of place into the other buffer),
+    indexed colour (colormap[index[id]]), and disc markers of radius 1, 2
+    and 4 pixels.  Per-frame CUDA events, L2 flushed by a 512 MB read."""
+    import torch
+    from paper_2504_20937_b300.api import Context
+    dev = torch.cuda.current_device()
+    flush = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sink = torch.zeros((), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+
+    def time_frames(ctx, step):
+        ms = []
+        for f in range(frames + 3):
+            ctx.set_camera(sc.eye(f), CENTRE, UP, sc.fovy_deg, sc.znear, sc.zfar)
+            sink.copy_(flush.sum())
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(ctx)
+            b.record(stream)
+            b.synchronize()
+            if f >= 3:
+                ms.append(a.elapsed_time(b))
+        m = statistics.mean(ms)
+        return {"ms_per_frame": m, "points_per_s": sc.n / (m / 1e3), "p99_ms": float(np.percentile(ms, 99))}
+
+    cases = [("pingpong", 0.0, False, True), ("indexed_colour", 0.0, True, False)]
+    cases += [(f"disc_r{r:g}", r, False, False) for r in (1.0, 2.0, 4.0)]
+    for name, radius, indexed, pingpong in cases:
+        with Context(sc.W, sc.H) as ctx:
+            if pingpong:
+                ctx.alloc_pingpong(sc.n, "f32")[0].copy_(torch.from_numpy(stored))
+            else:
+                ctx.alloc_points(sc.n, "f32").copy_(torch.from_numpy(stored))
+            if indexed:
+                idx, cm = ctx.alloc_indexed_colors(9)
+                idx.copy_(torch.arange(sc.n, dtype=torch.int32, device=dev) % 9)
+                cm.copy_(torch.arange(9, dtype=torch.int32, device=dev) * 0x1C1C1C)
+            ctx.set_sim(sc.philox_seed, 0, sc.amplitude, 0)
+            ctx.set_marker(radius)
+            torch.cuda.synchronize()
+            step = (lambda c: c.step_and_render_pingpong(stream)) if pingpong else (lambda c: c.step_and_render(stream))
+            res[name] = time_frames(ctx, step)
     return res
 
 

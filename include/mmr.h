@@ -97,6 +97,26 @@ MMR_API mmr_status mmr_alloc_points(mmr_ctx *ctx, uint64_t n, int dtype, void **
  * without it every point takes the default colour (Sec. 4.1: one colour). */
 MMR_API mmr_status mmr_alloc_colors(mmr_ctx *ctx, uint32_t **dev_colors);
 
+/* Ping-pong buffers (the paper's alternating read/write buffers, Sec. 3.4
+ * and Listing 2): allocate two point buffers of n points instead of one and
+ * return both device pointers (same layout and ownership as
+ * mmr_alloc_points; buffer 0 starts visible).  A simulation that reads one
+ * state and writes the next uses them in turn; mmr_set_visible picks the
+ * buffer mmr_render and mmr_step_and_render use (the paper's
+ * toggleVisibility).  MMR_ERR_STATE if the context already has points. */
+MMR_API mmr_status mmr_alloc_pingpong(mmr_ctx *ctx, uint64_t n, int dtype, void **dev_a, void **dev_b);
+MMR_API mmr_status mmr_set_visible(mmr_ctx *ctx, int which);
+MMR_API mmr_status mmr_get_visible(const mmr_ctx *ctx, int *which);
+
+/* Indexed colour (the paper's colour property read through an index buffer,
+ * Sec. 3.2.2, Listings 3 and 6): allocate a per-point index buffer (n uint32,
+ * zero-filled) and a colormap (ncolors RGBA8, 1..2^24, white) and return both
+ * device pointers.  Once allocated, a covered pixel is coloured
+ * colormap[index[id]]; an index >= ncolors takes the default colour.  Takes
+ * precedence over mmr_alloc_colors. */
+MMR_API mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint32_t **dev_index,
+                                            uint32_t **dev_colormap);
+
 /* ---- view and simulation parameters --------------------------------------- */
 
 /* Camera (the paper's interactive camera, Sec. 1): right-handed look-at from
@@ -120,6 +140,13 @@ MMR_API mmr_status mmr_get_matrix(const mmr_ctx *ctx, float m[16]);
  * step index is first_step.  0 <= amplitude <= 1, finite. */
 MMR_API mmr_status mmr_set_sim(mmr_ctx *ctx, uint64_t seed, uint32_t cloud, float amplitude,
                        uint32_t first_step);
+
+/* Marker shape.  radius_px = 0 (default): each point covers the one pixel it
+ * projects into.  0.5 <= radius_px <= 64: front-facing disc markers of the
+ * same size for all points (Sec. 4.1): a point covers every pixel whose
+ * centre lies within radius_px of its projected position (computed in FP32
+ * in a fixed order), all at the point's depth. */
+MMR_API mmr_status mmr_set_marker(mmr_ctx *ctx, float radius_px);
 
 /* Default point colour (no colour buffer) and background colour, RGBA8. */
 MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background);
@@ -146,6 +173,13 @@ MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, in
  * also clears the other depth-id buffer for the next frame.  Advances the
  * step counter.  Requires points and a camera. */
 MMR_API mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream);
+
+/* One frame out of place (ping-pong): read the visible buffer, write the
+ * displaced positions into the other one, render them and make that buffer
+ * visible.  The visible state and the frame equal those of
+ * mmr_step_and_render; the previous state stays untouched in the other
+ * buffer.  Requires mmr_alloc_pingpong. */
+MMR_API mmr_status mmr_step_and_render_pingpong(mmr_ctx *ctx, void *stream);
 
 /* Displace only (advances the step counter). */
 MMR_API mmr_status mmr_displace(mmr_ctx *ctx, void *stream);

@@ -52,6 +52,8 @@ _sig("orc_splat_f32", None, _f32p, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_floa
      C.c_uint32, _u64p)
 _sig("orc_splat_h16", None, _u16p, C.c_int, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_float, C.c_float,
      C.c_uint32, _u64p)
+_sig("orc_splat_disc_f32", None, _f32p, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
+     C.c_uint32, _u64p)
 _sig("orc_resolve", None, _u64p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_uint32, _u32p)
 
 EMPTY_KEY = np.uint64(0xFFFFFFFFFFFFFFFF)
@@ -191,6 +193,20 @@ def splat(pos, dtype, M32, W, H, znear, zfar, keybuf, id_base=0):
     else:
         _lib.orc_splat_h16(np.ascontiguousarray(pos, np.uint16).reshape(-1), KIND[dtype], pos.shape[0],
                            M, W, H, znear, zfar, id_base, keybuf)
+
+
+def splat_disc(pos, M32, W, H, znear, zfar, radius, keybuf, id_base=0):
+    """Disc markers of `radius` pixels (FP32 positions): per-pixel min of the
+    keys of all points whose disc covers the pixel centre."""
+    _lib.orc_splat_disc_f32(np.ascontiguousarray(pos, np.float32).reshape(-1), pos.shape[0],
+                            np.ascontiguousarray(M32, np.float32).reshape(-1), W, H, znear, zfar, radius, id_base,
+                            keybuf)
+
+
+def render_disc(pos, M32, W, H, znear, zfar, radius, colors=None, color=0xFFFFFFFF, background=0):
+    keys = empty_keys(W, H)
+    splat_disc(pos, M32, W, H, znear, zfar, radius, keys)
+    return keys, resolve(keys, colors, color, background)
 
 
 def resolve(keybuf, colors=None, color=0xFFFFFFFF, background=0):

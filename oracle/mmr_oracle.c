@@ -404,6 +404,62 @@ void orc_splat_h16(const uint16_t *pos, int kind, uint64_t n, const float M[16],
     }
 }
 
+/* Disc markers of radius r pixels (the paper's front-facing disc markers,
+ * Sec. 4.1): the point's key goes to every pixel whose centre (px + 1/2,
+ * py + 1/2) lies within r of the projected point (sx, sy):
+ *   dx = (px + 1/2) - sx, dy = (py + 1/2) - sy, covered iff dx*dx + dy*dy <= r*r
+ * in FP32, in that order.  The candidate pixels are those of the box
+ * [sx - r - 1, sx + r + 1] x [sy - r - 1, sy + r + 1] clipped to the frame; the
+ * exact test decides.  Depth and id as for 1-px points. */
+static int screen_f32(const float M[16], float x, float y, float z, float halfW, float halfH, float znear, float zfar,
+                      float *sx, float *sy, float *cw_out)
+{
+    float cx = ((M[0] * x + M[1] * y) + M[2] * z) + M[3];
+    float cy = ((M[4] * x + M[5] * y) + M[6] * z) + M[7];
+    float cw = ((M[12] * x + M[13] * y) + M[14] * z) + M[15];
+    if (!(cw > znear && cw < zfar))
+        return 0;
+    float nx = cx / cw;
+    float ny = cy / cw;
+    *sx = (nx + 1.0f) * halfW;
+    *sy = (1.0f - ny) * halfH;
+    *cw_out = cw;
+    return 1;
+}
+
+void orc_splat_disc_f32(const float *pos, uint64_t n, const float M[16], int W, int H, float znear, float zfar,
+                        float radius, uint32_t id_base, uint64_t *keybuf)
+{
+    const float r2 = radius * radius;
+    const float halfW = 0.5f * (float)W, halfH = 0.5f * (float)H;
+    for (uint64_t i = 0; i < n; ++i) {
+        float sx, sy, cw;
+        if (!screen_f32(M, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], halfW, halfH, znear, zfar, &sx, &sy, &cw))
+            continue;
+        float xa = sx - radius - 1.0f, xb = sx + radius + 1.0f;
+        float ya = sy - radius - 1.0f, yb = sy + radius + 1.0f;
+        if (xa < 0.0f) xa = 0.0f;
+        if (ya < 0.0f) ya = 0.0f;
+        if (xb > (float)(W - 1)) xb = (float)(W - 1);
+        if (yb > (float)(H - 1)) yb = (float)(H - 1);
+        if (!(xa <= xb && ya <= yb))
+            continue;
+        uint64_t key = ((uint64_t)f32_bits(cw) << 32) | (uint64_t)(uint32_t)(id_base + (uint32_t)i);
+        for (int py = (int)ya; py <= (int)yb; ++py) {
+            float dy = ((float)py + 0.5f) - sy;
+            for (int px = (int)xa; px <= (int)xb; ++px) {
+                float dx = ((float)px + 0.5f) - sx;
+                float d2 = dx * dx + dy * dy;
+                if (d2 <= r2) {
+                    uint64_t *k = &keybuf[(uint64_t)py * (uint64_t)W + (uint64_t)px];
+                    if (key < *k)
+                        *k = key;
+                }
+            }
+        }
+    }
+}
+
 /* Resolve: key -> RGBA8.  colors == NULL means every point takes `color`. */
 void orc_resolve(const uint64_t *keybuf, uint64_t npx, const uint32_t *colors, uint32_t color,
                  uint32_t background, uint32_t *rgba)

@@ -36,11 +36,17 @@ SIGNATURES = {
     "mmr_status_string": (C.c_char_p, [_i]),
     "mmr_alloc_points": (_i, [_vp, _u64, _i, C.POINTER(_vp)]),
     "mmr_alloc_colors": (_i, [_vp, C.POINTER(_vp)]),
+    "mmr_alloc_pingpong": (_i, [_vp, _u64, _i, C.POINTER(_vp), C.POINTER(_vp)]),
+    "mmr_set_visible": (_i, [_vp, _i]),
+    "mmr_get_visible": (_i, [_vp, C.POINTER(_i)]),
+    "mmr_step_and_render_pingpong": (_i, [_vp, _vp]),
+    "mmr_alloc_indexed_colors": (_i, [_vp, _u32, C.POINTER(_vp), C.POINTER(_vp)]),
     "mmr_set_camera": (_i, [_vp, _d3, _d3, _d3, _d, _d, _d]),
     "mmr_set_matrix": (_i, [_vp, _f16, _f, _f]),
     "mmr_get_matrix": (_i, [_vp, _f16]),
     "mmr_set_sim": (_i, [_vp, _u64, _u32, _f, _u32]),
     "mmr_set_style": (_i, [_vp, _u32, _u32]),
+    "mmr_set_marker": (_i, [_vp, _f]),
     "mmr_set_launch": (_i, [_vp, _i, _i, _i]),
     "mmr_step_and_render": (_i, [_vp, _vp]),
     "mmr_displace": (_i, [_vp, _vp]),

@@ -80,8 +80,39 @@ class Context:
         self._points = device_view(p.value, (n, 3), typestr)
         return self._points
 
+    def alloc_pingpong(self, n: int, dtype: str = "f32"):
+        """Two point buffers (views) for read-one / write-the-other simulations."""
+        a, b = C.c_void_p(), C.c_void_p()
+        self._check(self._lib.mmr_alloc_pingpong(self._h, n, DTYPE_CODE[dtype], C.byref(a), C.byref(b)))
+        self.n, self.dtype = n, dtype
+        typestr = _TORCH_VIEW[dtype][1]
+        self._pp = (device_view(a.value, (n, 3), typestr), device_view(b.value, (n, 3), typestr))
+        self._points = self._pp[0]
+        return self._pp
+
+    def set_visible(self, which: int):
+        self._check(self._lib.mmr_set_visible(self._h, which))
+
+    @property
+    def visible(self) -> int:
+        w = C.c_int()
+        self._check(self._lib.mmr_get_visible(self._h, C.byref(w)))
+        return w.value
+
+    def step_and_render_pingpong(self, stream=None):
+        self._check(self._lib.mmr_step_and_render_pingpong(self._h, stream_handle(stream)))
+
+    def alloc_indexed_colors(self, ncolors: int):
+        """(index int32[n] view, colormap int32[ncolors] view)."""
+        i, m = C.c_void_p(), C.c_void_p()
+        self._check(self._lib.mmr_alloc_indexed_colors(self._h, ncolors, C.byref(i), C.byref(m)))
+        return device_view(i.value, (self.n,), "<i4"), device_view(m.value, (ncolors,), "<i4")
+
     @property
     def points(self) -> torch.Tensor:
+        """The visible point buffer."""
+        if getattr(self, "_pp", None) is not None:
+            return self._pp[self.visible]
         return self._points
 
     def alloc_colors(self) -> torch.Tensor:
@@ -108,6 +139,10 @@ class Context:
 
     def set_style(self, color: int = 0xFFFFFFFF, background: int = 0):
         self._check(self._lib.mmr_set_style(self._h, color, background))
+
+    def set_marker(self, radius_px: float = 0.0):
+        """0: 1-px points; 0.5..64: disc markers of that radius in pixels."""
+        self._check(self._lib.mmr_set_marker(self._h, radius_px))
 
     def set_launch(self, threads: int = 256, ctas_per_sm: int = 0, kernel: int = 0):
         """kernel 0: grid-stride (ctas_per_sm 0 = one thread per group, else

@@ -11,6 +11,7 @@
 #include "../../include/mmr.h"
 #include "mmr_device.cuh"
 #include "mmr_internal.h"
+#include "mmr_resolve.cuh"
 
 namespace {
 
@@ -31,11 +32,15 @@ struct mmr_ctx {
     uint32_t *rgba = nullptr;
     uint32_t *d_err = nullptr;    // device error word (bounded waits that gave up)
 
-    void *points = nullptr;
+    void *buf[2] = {nullptr, nullptr};   // point buffers; buf[1] only with ping-pong
+    int visible = 0;                     // the buffer holding the current state (rendered)
     uint64_t n = 0;
     int dtype = 0;
     uint64_t point_bytes = 0;
     uint32_t *colors = nullptr;
+    uint32_t *index = nullptr;           // indexed colour: colormap[index[id]]
+    uint32_t *colormap = nullptr;
+    uint32_t ncolors = 0;
 
     // round-trip baseline buffers (allocated on first use)
     void *rt_device = nullptr;
@@ -52,6 +57,7 @@ struct mmr_ctx {
     uint32_t step = 0;
     uint32_t color = 0xFFFFFFFFu;
     uint32_t background = 0u;
+    float disc_r = 0.0f;          // 0: 1-px points; else disc markers of this radius (pixels)
 
     bool timing = false;
     bool timed_frame = false;
@@ -147,13 +153,20 @@ mmr::PointParams point_params(const mmr_ctx *c)
     P.cloud = c->cloud;
     P.amplitude = c->amplitude;
     P.id_base = 0;
+    P.disc_r = c->disc_r;
+    P.disc_r2 = c->disc_r * c->disc_r;
     mmr::philox_prepare(P);
     return P;
 }
 
+mmr::Palette palette(const mmr_ctx *c)
+{
+    return mmr::Palette{c->colors, c->index, c->colormap, c->ncolors, c->color, c->background};
+}
+
 mmr_status check_frame_ready(mmr_ctx *c, bool need_cam)
 {
-    if (!c->points)
+    if (!c->buf[0])
         return fail(c, MMR_ERR_STATE, "no points allocated (call mmr_alloc_points first)");
     if (need_cam && !c->have_cam)
         return fail(c, MMR_ERR_STATE, "no camera set (call mmr_set_camera or mmr_set_matrix first)");
@@ -164,29 +177,32 @@ bool uses_tma(const mmr::LaunchShape &ls) { return ls.kernel == MMR_KERNEL_TMA; 
 
 // The TMA-staged persistent kernel when the launch shape allows it (the
 // context's buffers are padded to whole groups), else the grid-stride one.
-cudaError_t launch_point_kernel(mmr_ctx *c, void *pos, const mmr::PointParams &P, bool displace, bool splat,
-                                cudaStream_t s)
+cudaError_t launch_point_kernel(mmr_ctx *c, const void *src, void *dst, const mmr::PointParams &P, bool displace,
+                                bool splat, cudaStream_t s)
 {
+    if (splat && c->disc_r > 0.0f)
+        return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, s);
     if (uses_tma(c->launch))
-        return mmr::launch_points_tma(c->dtype, pos, (uint32_t)c->n, P, displace, splat, c->d_err, c->launch, s);
-    return mmr::launch_points(c->dtype, pos, (uint32_t)c->n, P, displace, splat, c->launch, s);
+        return mmr::launch_points_tma(c->dtype, src, dst, (uint32_t)c->n, P, displace, splat, c->d_err, c->launch,
+                                      s);
+    return mmr::launch_points(c->dtype, src, dst, (uint32_t)c->n, P, displace, splat, c->launch, s);
 }
 
-// Render the current point buffer `pos` into the splat key buffer, then
-// resolve and flip buffers.  `displace` fuses the step into the same kernel.
-mmr_status frame(mmr_ctx *c, void *pos, bool displace, cudaStream_t s)
+// Render the positions in `src` into the splat key buffer (displacing them
+// into `dst` first when `displace`), then resolve and flip key buffers.
+mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStream_t s)
 {
     mmr::PointParams P = point_params(c);
     if (c->timing)
         cudaEventRecord(c->ev[0], s);
-    cudaError_t e = launch_point_kernel(c, pos, P, displace, true, s);
+    cudaError_t e = launch_point_kernel(c, src, dst, P, displace, true, s);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "point kernel launch");
     if (c->timing)
         cudaEventRecord(c->ev[1], s);
     const int cur = c->splat_buf;
-    e = mmr::launch_resolve(c->keys[cur], c->keys[cur ^ 1], c->rgba, c->colors, (uint32_t)frame_px(c),
-                            c->color, c->background, c->launch, s);
+    e = mmr::launch_resolve(c->keys[cur], c->keys[cur ^ 1], c->rgba, palette(c), (uint32_t)frame_px(c), c->launch,
+                            s);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "resolve kernel launch");
     if (c->timing) {
@@ -338,8 +354,11 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     dev_free(ctx, (void **)&ctx->keys[1], frame_px(ctx) * 8);
     dev_free(ctx, (void **)&ctx->rgba, frame_px(ctx) * 4);
     dev_free(ctx, (void **)&ctx->d_err, 4);
-    dev_free(ctx, &ctx->points, storage_bytes(ctx->n, ctx->dtype));
+    dev_free(ctx, &ctx->buf[0], storage_bytes(ctx->n, ctx->dtype));
+    dev_free(ctx, &ctx->buf[1], storage_bytes(ctx->n, ctx->dtype));
     dev_free(ctx, (void **)&ctx->colors, ctx->n * 4);
+    dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
+    dev_free(ctx, (void **)&ctx->colormap, (uint64_t)ctx->ncolors * 4);
     dev_free(ctx, &ctx->rt_device, storage_bytes(ctx->n, ctx->dtype));
     if (ctx->rt_host) {
         if (ctx->rt_host_pinned == 1)
@@ -354,33 +373,120 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     return MMR_OK;
 }
 
+static mmr_status alloc_point_buffers(mmr_ctx *ctx, uint64_t n, int dtype, int count, const char *who)
+{
+    if (n == 0 || n >= (1ull << 32))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "%s: n=%llu outside 1..2^32-1", who, (unsigned long long)n);
+    if (dtype != MMR_F32x3 && dtype != MMR_F16x3 && dtype != MMR_BF16x3)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "%s: unknown dtype %d", who, dtype);
+    if (ctx->buf[0])
+        return fail(ctx, MMR_ERR_STATE, "%s: this context already has points", who);
+    const uint64_t bytes = storage_bytes(n, dtype);
+    for (int k = 0; k < count; ++k) {
+        mmr_status st = dev_alloc(ctx, &ctx->buf[k], bytes, k ? "second point buffer" : "point buffer");
+        cudaError_t e = st == MMR_OK ? cudaMemset(ctx->buf[k], 0, bytes) : cudaSuccess;
+        if (st == MMR_OK && e == cudaSuccess)
+            e = cudaDeviceSynchronize();
+        if (st != MMR_OK || e != cudaSuccess) {
+            if (st == MMR_OK)
+                st = cuda_fail(ctx, e, "clearing points");
+            dev_free(ctx, &ctx->buf[0], bytes);
+            dev_free(ctx, &ctx->buf[1], bytes);
+            return st;
+        }
+    }
+    ctx->n = n;
+    ctx->dtype = dtype;
+    ctx->point_bytes = n * bytes_per_point(dtype);
+    ctx->visible = 0;
+    return MMR_OK;
+}
+
 mmr_status mmr_alloc_points(mmr_ctx *ctx, uint64_t n, int dtype, void **dev_ptr)
 {
     if (!ctx || !dev_ptr)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_points: NULL argument");
     *dev_ptr = nullptr;
-    if (n == 0 || n >= (1ull << 32))
-        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_points: n=%llu outside 1..2^32-1",
-                    (unsigned long long)n);
-    if (dtype != MMR_F32x3 && dtype != MMR_F16x3 && dtype != MMR_BF16x3)
-        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_points: unknown dtype %d", dtype);
-    if (ctx->points)
-        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_points: this context already has points");
-    const uint64_t bytes = storage_bytes(n, dtype);
-    mmr_status st = dev_alloc(ctx, &ctx->points, bytes, "point buffer");
+    mmr_status st = alloc_point_buffers(ctx, n, dtype, 1, "mmr_alloc_points");
+    if (st == MMR_OK)
+        *dev_ptr = ctx->buf[0];
+    return st;
+}
+
+mmr_status mmr_alloc_pingpong(mmr_ctx *ctx, uint64_t n, int dtype, void **dev_a, void **dev_b)
+{
+    if (!ctx || !dev_a || !dev_b)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_pingpong: NULL argument");
+    *dev_a = *dev_b = nullptr;
+    mmr_status st = alloc_point_buffers(ctx, n, dtype, 2, "mmr_alloc_pingpong");
+    if (st == MMR_OK) {
+        *dev_a = ctx->buf[0];
+        *dev_b = ctx->buf[1];
+    }
+    return st;
+}
+
+mmr_status mmr_set_visible(mmr_ctx *ctx, int which)
+{
+    if (!ctx || (which != 0 && which != 1))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_visible: which must be 0 or 1");
+    if (!ctx->buf[which])
+        return fail(ctx, MMR_ERR_STATE, "mmr_set_visible: buffer %d not allocated (use mmr_alloc_pingpong)", which);
+    ctx->visible = which;
+    return MMR_OK;
+}
+
+mmr_status mmr_get_visible(const mmr_ctx *ctx, int *which)
+{
+    if (!ctx || !which)
+        return MMR_ERR_INVALID_ARG;
+    *which = ctx->visible;
+    return MMR_OK;
+}
+
+mmr_status mmr_step_and_render_pingpong(mmr_ctx *ctx, void *stream)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = check_frame_ready(ctx, true);
     if (st != MMR_OK)
         return st;
-    cudaError_t e = cudaMemset(ctx->points, 0, bytes);
+    if (!ctx->buf[1])
+        return fail(ctx, MMR_ERR_STATE, "mmr_step_and_render_pingpong: no second buffer (use mmr_alloc_pingpong)");
+    const int r = ctx->visible;
+    st = frame(ctx, ctx->buf[r], ctx->buf[r ^ 1], true, (cudaStream_t)stream);
+    if (st == MMR_OK)
+        ctx->visible = r ^ 1;
+    return st;
+}
+
+mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint32_t **dev_index, uint32_t **dev_colormap)
+{
+    if (!ctx || !dev_index || !dev_colormap || ncolors == 0 || ncolors > (1u << 24))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_indexed_colors: bad argument (1 <= ncolors <= 2^24)");
+    *dev_index = nullptr;
+    *dev_colormap = nullptr;
+    if (!ctx->buf[0])
+        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_indexed_colors: allocate points first");
+    if (ctx->index)
+        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_indexed_colors: already allocated");
+    mmr_status st = dev_alloc(ctx, (void **)&ctx->index, ctx->n * 4, "colour index buffer");
+    if (st == MMR_OK)
+        st = dev_alloc(ctx, (void **)&ctx->colormap, (uint64_t)ncolors * 4, "colormap");
+    if (st != MMR_OK) {
+        dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
+        return st;
+    }
+    ctx->ncolors = ncolors;
+    cudaError_t e = cudaMemset(ctx->index, 0, ctx->n * 4);
+    if (e == cudaSuccess)
+        e = cudaMemset(ctx->colormap, 0xff, (uint64_t)ncolors * 4);
     if (e == cudaSuccess)
         e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-        dev_free(ctx, &ctx->points, bytes);
-        return cuda_fail(ctx, e, "mmr_alloc_points: clearing");
-    }
-    ctx->n = n;
-    ctx->dtype = dtype;
-    ctx->point_bytes = n * bytes_per_point(dtype);
-    *dev_ptr = ctx->points;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_alloc_indexed_colors: clearing");
+    *dev_index = ctx->index;
+    *dev_colormap = ctx->colormap;
     return MMR_OK;
 }
 
@@ -389,7 +495,7 @@ mmr_status mmr_alloc_colors(mmr_ctx *ctx, uint32_t **dev_colors)
     if (!ctx || !dev_colors)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_colors: NULL argument");
     *dev_colors = nullptr;
-    if (!ctx->points)
+    if (!ctx->buf[0])
         return fail(ctx, MMR_ERR_STATE, "mmr_alloc_colors: allocate points first");
     if (!ctx->colors) {
         mmr_status st = dev_alloc(ctx, (void **)&ctx->colors, ctx->n * 4, "colour buffer");
@@ -471,6 +577,16 @@ mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background)
     return MMR_OK;
 }
 
+mmr_status mmr_set_marker(mmr_ctx *ctx, float radius_px)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (!(radius_px == 0.0f || (radius_px >= 0.5f && radius_px <= 64.0f)))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_marker: radius must be 0 (1-px points) or in [0.5, 64]");
+    ctx->disc_r = radius_px;
+    return MMR_OK;
+}
+
 mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel)
 {
     if (!ctx)
@@ -496,7 +612,8 @@ mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream)
     mmr_status st = check_frame_ready(ctx, true);
     if (st != MMR_OK)
         return st;
-    return frame(ctx, ctx->points, true, (cudaStream_t)stream);
+    void *cur = ctx->buf[ctx->visible];
+    return frame(ctx, cur, cur, true, (cudaStream_t)stream);
 }
 
 mmr_status mmr_render(mmr_ctx *ctx, void *stream)
@@ -506,7 +623,7 @@ mmr_status mmr_render(mmr_ctx *ctx, void *stream)
     mmr_status st = check_frame_ready(ctx, true);
     if (st != MMR_OK)
         return st;
-    return frame(ctx, ctx->points, false, (cudaStream_t)stream);
+    return frame(ctx, ctx->buf[ctx->visible], nullptr, false, (cudaStream_t)stream);
 }
 
 mmr_status mmr_displace(mmr_ctx *ctx, void *stream)
@@ -517,7 +634,8 @@ mmr_status mmr_displace(mmr_ctx *ctx, void *stream)
     if (st != MMR_OK)
         return st;
     mmr::PointParams P = point_params(ctx);
-    cudaError_t e = launch_point_kernel(ctx, ctx->points, P, true, false, (cudaStream_t)stream);
+    void *cur = ctx->buf[ctx->visible];
+    cudaError_t e = launch_point_kernel(ctx, cur, cur, P, true, false, (cudaStream_t)stream);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "displace kernel launch");
     ctx->step += 1;
@@ -568,12 +686,13 @@ mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int pinned_
     st = mmr_displace(ctx, stream);
     if (st != MMR_OK)
         return st;
-    cudaError_t e = cudaMemcpyAsync(ctx->rt_host, ctx->points, ctx->point_bytes, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(ctx->rt_host, ctx->buf[ctx->visible], ctx->point_bytes, cudaMemcpyDeviceToHost,
+                                    s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->rt_device, ctx->rt_host, ctx->point_bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "round-trip copies");
-    return frame(ctx, ctx->rt_device, false, s);
+    return frame(ctx, ctx->rt_device, nullptr, false, s);
 }
 
 mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **depth_id)

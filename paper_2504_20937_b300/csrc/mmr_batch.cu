@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_points_kernel(BatchTab
                 process_words<DT, true, true>(q, g * Group<DT>::kPoints, Group<DT>::kPoints, P);
                 store_words(cl.pos, g, q);
             } else {
-                process_tail<DT, true, true>(cl.pos, n, g * Group<DT>::kPoints, P);
+                process_tail<DT, true, true>(cl.pos, cl.pos, n, g * Group<DT>::kPoints, P);
             }
         }
     }
@@ -112,10 +112,11 @@ __global__ void batch_resolve_kernel(BatchTables T)
         unsigned long long *next = cl.keys[buf ^ 1];
         const uint32_t quads = cl.npx / 4;
         const uint32_t end = min(ch.y + T.chunk_quads, quads);
+        const Palette pal{nullptr, nullptr, nullptr, 0u, cl.color, cl.background};
         for (uint32_t q = ch.y + threadIdx.x; q < end; q += blockDim.x)
-            resolve_quad(keys, next, cl.rgba, nullptr, q, cl.color, cl.background);
+            resolve_quad(keys, next, cl.rgba, pal, q);
         if (end == quads && quads * 4 + threadIdx.x < cl.npx)
-            resolve_pixel(keys, next, cl.rgba, nullptr, quads * 4 + threadIdx.x, cl.color, cl.background);
+            resolve_pixel(keys, next, cl.rgba, pal, quads * 4 + threadIdx.x);
     }
 }
 

@@ -7,6 +7,7 @@
 namespace mmr {
 
 struct PointParams;
+struct Palette;
 
 struct LaunchShape {
     int threads = 256;       // threads per block
@@ -15,22 +16,27 @@ struct LaunchShape {
     int kernel = 0;          // 0: grid-stride point kernel, 1: TMA-staged
 };
 
-cudaError_t launch_points(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
+// Point kernels read positions from src and write displaced ones to dst
+// (src == dst for an in-place step).
+cudaError_t launch_points(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
                           bool splat, const LaunchShape &ls, cudaStream_t s);
+
+// Disc markers of radius P.disc_r pixels (grid-stride, 64 threads).
+cudaError_t launch_points_disc(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                               bool displace, cudaStream_t s);
 
 // TMA-staged persistent variant (threads 128, 256 or 512; grid =
 // sm_count * ctas_per_sm CTAs).  The buffer must be padded to whole 48-byte
 // groups.  A timed-out wait sets *err (device word) to a non-zero value.
-cudaError_t launch_points_tma(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
-                              uint32_t *err, const LaunchShape &ls, cudaStream_t s);
+cudaError_t launch_points_tma(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                              bool displace, bool splat, uint32_t *err, const LaunchShape &ls, cudaStream_t s);
 
 // One CTA that waits on an mbarrier nothing arrives on, for max_cycles, then
 // sets *err like a point kernel whose bulk copy never completed.
 cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cudaStream_t s);
 
-cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys,
-                           uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,
-                           uint32_t background, const LaunchShape &ls, cudaStream_t s);
+cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
+                           const Palette &pal, uint32_t npx, const LaunchShape &ls, cudaStream_t s);
 
 // Message returned by mmr_last_error(NULL) on this thread.
 void set_process_error(const char *msg);

@@ -16,9 +16,11 @@ namespace mmr {
 // Grid-stride over 48-byte point groups.  With a persistent grid (fewer
 // threads than groups) each thread prefetches its next group into registers
 // before working on the current one, so a load is always in flight while the
-// thread computes; with one thread per group the loop runs once.
+// thread computes; with one thread per group the loop runs once.  Positions
+// are read from src and the displaced ones written to dst: the same buffer
+// for an in-place step, the other ping-pong buffer otherwise.
 template <int DT, bool kDisplace, bool kSplat>
-__global__ void points_kernel(void *__restrict__ pos, uint32_t n, PointParams P)
+__global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParams P)
 {
     constexpr int G = Group<DT>::kPoints;
     const uint32_t full = n / G;
@@ -27,20 +29,100 @@ __global__ void points_kernel(void *__restrict__ pos, uint32_t n, PointParams P)
     uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     uint4 next[3];
     if (g < full)
-        load_words(pos, g, next);
+        load_words(src, g, next);
     while (g < groups) {
         const uint32_t gn = g + stride;
         if (g < full) {
             uint4 q[3] = {next[0], next[1], next[2]};
             if (gn < full)
-                load_words(pos, gn, next);
+                load_words(src, gn, next);
             process_words<DT, kDisplace, kSplat>(q, g * G, G, P);
             if constexpr (kDisplace)
-                store_words(pos, g, q);
+                store_words(dst, g, q);
         } else {
-            process_tail<DT, kDisplace, kSplat>(pos, n, g * G, P);
+            process_tail<DT, kDisplace, kSplat>(src, dst, n, g * G, P);
         }
         g = gn;
+    }
+}
+
+// Disc markers: as points_kernel (one thread per 48-byte group), each point
+// splatted as a disc of radius P.disc_r pixels instead of one pixel.
+template <int DT, bool kDisplace>
+__global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, PointParams P)
+{
+    constexpr int G = Group<DT>::kPoints;
+    const uint32_t full = n / G;
+    const uint32_t groups = groups_of<DT>(n);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
+        const uint32_t i0 = g * G;
+        const uint32_t count = min((uint32_t)G, n - i0);
+        uint4 q[3];
+        float v[3 * G];
+        if (g < full) {
+            load_words(src, g, q);
+#pragma unroll
+            for (int k = 0; k < 3 * G; ++k)
+                v[k] = word_coord<DT>(q, k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3 * G; ++k)
+                v[k] = (uint32_t)(k / 3) < count ? load_coord<DT>(src, 3ull * i0 + k) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if ((uint32_t)j >= count)
+                continue;
+            if constexpr (kDisplace) {
+                displace_point(v[3 * j], v[3 * j + 1], v[3 * j + 2], i0 + j, P);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    v[3 * j + c] = storage_round<DT>(v[3 * j + c]);
+            }
+            float sx, sy, cw;
+            if (project_screen(v[3 * j], v[3 * j + 1], v[3 * j + 2], P, sx, sy, cw))
+                splat_disc(sx, sy, ((unsigned long long)__float_as_uint(cw) << 32) | (P.id_base + i0 + j), P);
+        }
+        if constexpr (kDisplace) {
+            if (g < full) {
+#pragma unroll
+                for (int k = 0; k < 3 * G; ++k)
+                    set_word_coord<DT>(q, k, v[k]);
+                store_words(dst, g, q);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3 * G; ++k)
+                    if ((uint32_t)k < 3 * count)
+                        store_coord<DT>(dst, 3ull * i0 + k, v[k]);
+            }
+        }
+    }
+}
+
+template <int DT>
+static cudaError_t launch_disc_dt(const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
+                                  cudaStream_t s)
+{
+    const uint64_t groups = groups_of<DT>(n);
+    const int grid = (int)std::max<uint64_t>(1, (groups + 63) / 64);
+    if (displace)
+        points_disc_kernel<DT, true><<<grid, 64, 0, s>>>(src, dst, n, P);
+    else
+        points_disc_kernel<DT, false><<<grid, 64, 0, s>>>(src, dst, n, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points_disc(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                               bool displace, cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    switch (dtype) {
+    case kF32: return launch_disc_dt<kF32>(src, dst, n, P, displace, s);
+    case kF16: return launch_disc_dt<kF16>(src, dst, n, P, displace, s);
+    case kBF16: return launch_disc_dt<kBF16>(src, dst, n, P, displace, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 
@@ -66,7 +148,7 @@ constexpr uint32_t tma_smem_bytes()
 }
 
 template <int DT, bool kDisplace, bool kSplat, int kThreads>
-__global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__ pos, uint32_t n, PointParams P,
+__global__ void __launch_bounds__(kThreads) points_tma_kernel(const void *src, void *dst, uint32_t n, PointParams P,
                                                               uint32_t *__restrict__ err)
 {
     constexpr int G = Group<DT>::kPoints;
@@ -79,7 +161,8 @@ __global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__
     if (blockIdx.x >= tiles)
         return;
     const uint32_t my_tiles = (tiles - 1 - blockIdx.x) / gridDim.x + 1;
-    char *gbase = static_cast<char *>(pos);
+    const char *gsrc = static_cast<const char *>(src);
+    char *gdst = static_cast<char *>(dst);
     auto tile_of = [&](uint32_t k) { return blockIdx.x + k * gridDim.x; };
     auto bytes_of = [&](uint32_t tile) { return min((uint32_t)kThreads, total_groups - tile * kThreads) * 48u; };
 
@@ -90,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__
         for (uint32_t k = 0; k < my_tiles && k < (uint32_t)kTmaStages; ++k) {
             const uint32_t tile = tile_of(k), bytes = bytes_of(tile), bar = smem_addr(&bars[k]);
             mbar_arrive_expect_tx(bar, bytes);
-            bulk_load(smem_addr(smem + k * kTileBytes), gbase + (size_t)tile * kTileBytes, bytes, bar);
+            bulk_load(smem_addr(smem + k * kTileBytes), gsrc + (size_t)tile * kTileBytes, bytes, bar);
         }
     }
     __syncthreads();
@@ -127,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__
         }
         if (tid == 0) {
             if constexpr (kDisplace) {
-                bulk_store(gbase + (size_t)tile * kTileBytes, smem_addr(stage), bytes_of(tile));
+                bulk_store(gdst + (size_t)tile * kTileBytes, smem_addr(stage), bytes_of(tile));
                 bulk_commit();
             }
             const uint32_t kn = k + kTmaStages;
@@ -136,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) points_tma_kernel(void *__restrict__
                     bulk_wait_read_all();       // the store has left the stage
                 const uint32_t tn = tile_of(kn), bytes = bytes_of(tn), bar = smem_addr(&bars[st]);
                 mbar_arrive_expect_tx(bar, bytes);
-                bulk_load(smem_addr(stage), gbase + (size_t)tn * kTileBytes, bytes, bar);
+                bulk_load(smem_addr(stage), gsrc + (size_t)tn * kTileBytes, bytes, bar);
             }
         }
     }
@@ -172,16 +255,15 @@ cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cu
 // (npx not a multiple of 4) goes to the first threads.
 __global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
                                unsigned long long *__restrict__ next_keys,
-                               uint32_t *__restrict__ rgba, const uint32_t *__restrict__ colors,
-                               uint32_t npx, uint32_t color, uint32_t background)
+                               uint32_t *__restrict__ rgba, Palette pal, uint32_t npx)
 {
     const uint32_t quads = npx / 4;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     for (uint32_t q = t; q < quads; q += stride)
-        resolve_quad(keys, next_keys, rgba, colors, q, color, background);
+        resolve_quad(keys, next_keys, rgba, pal, q);
     if (quads * 4 + t < npx)
-        resolve_pixel(keys, next_keys, rgba, colors, quads * 4 + t, color, background);
+        resolve_pixel(keys, next_keys, rgba, pal, quads * 4 + t);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -199,23 +281,23 @@ static int grid_for(uint64_t work_items, const LaunchShape &ls)
 }
 
 template <int DT>
-static cudaError_t launch_points_dt(void *pos, uint32_t n, const PointParams &P, bool displace,
+static cudaError_t launch_points_dt(const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
                                     bool splat, const LaunchShape &ls, cudaStream_t s)
 {
     const uint64_t groups = groups_of<DT>(n);
     const int grid = grid_for(groups, ls);
     if (displace && splat)
-        points_kernel<DT, true, true><<<grid, ls.threads, 0, s>>>(pos, n, P);
+        points_kernel<DT, true, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
     else if (displace)
-        points_kernel<DT, true, false><<<grid, ls.threads, 0, s>>>(pos, n, P);
+        points_kernel<DT, true, false><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
     else
-        points_kernel<DT, false, true><<<grid, ls.threads, 0, s>>>(pos, n, P);
+        points_kernel<DT, false, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
     return cudaGetLastError();
 }
 
 template <int DT, bool kD, bool kS, int kT>
-static cudaError_t launch_tma_one(void *pos, uint32_t n, const PointParams &P, uint32_t *err, int ctas_per_sm,
-                                  int sm_count, cudaStream_t s)
+static cudaError_t launch_tma_one(const void *src, void *dst, uint32_t n, const PointParams &P, uint32_t *err,
+                                  int ctas_per_sm, int sm_count, cudaStream_t s)
 {
     constexpr uint32_t smem = tma_smem_bytes<kT>();
     static unsigned long long configured = 0;    // one bit per device ordinal
@@ -233,69 +315,69 @@ static cudaError_t launch_tma_one(void *pos, uint32_t n, const PointParams &P, u
     }
     const uint64_t tiles = (groups_of<DT>(n) + kT - 1) / kT;
     const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sm_count * ctas_per_sm);
-    points_tma_kernel<DT, kD, kS, kT><<<grid, kT, smem, s>>>(pos, n, P, err);
+    points_tma_kernel<DT, kD, kS, kT><<<grid, kT, smem, s>>>(src, dst, n, P, err);
     return cudaGetLastError();
 }
 
 template <int DT, int kT>
-static cudaError_t launch_tma_dt(void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
-                                 uint32_t *err, int ctas_per_sm, int sm_count, cudaStream_t s)
+static cudaError_t launch_tma_dt(const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
+                                 bool splat, uint32_t *err, int ctas_per_sm, int sm_count, cudaStream_t s)
 {
     if (displace && splat)
-        return launch_tma_one<DT, true, true, kT>(pos, n, P, err, ctas_per_sm, sm_count, s);
+        return launch_tma_one<DT, true, true, kT>(src, dst, n, P, err, ctas_per_sm, sm_count, s);
     if (displace)
-        return launch_tma_one<DT, true, false, kT>(pos, n, P, err, ctas_per_sm, sm_count, s);
-    return launch_tma_one<DT, false, true, kT>(pos, n, P, err, ctas_per_sm, sm_count, s);
+        return launch_tma_one<DT, true, false, kT>(src, dst, n, P, err, ctas_per_sm, sm_count, s);
+    return launch_tma_one<DT, false, true, kT>(src, dst, n, P, err, ctas_per_sm, sm_count, s);
 }
 
 template <int kT>
-static cudaError_t launch_tma_threads(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
-                                     bool splat, uint32_t *err, int ctas_per_sm, int sm_count, cudaStream_t s)
+static cudaError_t launch_tma_threads(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                                     bool displace, bool splat, uint32_t *err, int ctas_per_sm, int sm_count,
+                                     cudaStream_t s)
 {
     switch (dtype) {
-    case kF32: return launch_tma_dt<kF32, kT>(pos, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
-    case kF16: return launch_tma_dt<kF16, kT>(pos, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
-    case kBF16: return launch_tma_dt<kBF16, kT>(pos, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
+    case kF32: return launch_tma_dt<kF32, kT>(src, dst, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
+    case kF16: return launch_tma_dt<kF16, kT>(src, dst, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
+    case kBF16: return launch_tma_dt<kBF16, kT>(src, dst, n, P, displace, splat, err, ctas_per_sm, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_points_tma(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace, bool splat,
-                              uint32_t *err, const LaunchShape &ls, cudaStream_t s)
+cudaError_t launch_points_tma(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                              bool displace, bool splat, uint32_t *err, const LaunchShape &ls, cudaStream_t s)
 {
     if (n == 0)
         return cudaSuccess;
     const int ctas = ls.ctas_per_sm > 0 ? ls.ctas_per_sm : 1;
     switch (ls.threads) {
-    case 128: return launch_tma_threads<128>(dtype, pos, n, P, displace, splat, err, ctas, ls.sm_count, s);
-    case 256: return launch_tma_threads<256>(dtype, pos, n, P, displace, splat, err, ctas, ls.sm_count, s);
-    case 512: return launch_tma_threads<512>(dtype, pos, n, P, displace, splat, err, ctas, ls.sm_count, s);
+    case 128: return launch_tma_threads<128>(dtype, src, dst, n, P, displace, splat, err, ctas, ls.sm_count, s);
+    case 256: return launch_tma_threads<256>(dtype, src, dst, n, P, displace, splat, err, ctas, ls.sm_count, s);
+    case 512: return launch_tma_threads<512>(dtype, src, dst, n, P, displace, splat, err, ctas, ls.sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_points(int dtype, void *pos, uint32_t n, const PointParams &P, bool displace,
+cudaError_t launch_points(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
                           bool splat, const LaunchShape &ls, cudaStream_t s)
 {
     if (n == 0)
         return cudaSuccess;
     switch (dtype) {
-    case kF32: return launch_points_dt<kF32>(pos, n, P, displace, splat, ls, s);
-    case kF16: return launch_points_dt<kF16>(pos, n, P, displace, splat, ls, s);
-    case kBF16: return launch_points_dt<kBF16>(pos, n, P, displace, splat, ls, s);
+    case kF32: return launch_points_dt<kF32>(src, dst, n, P, displace, splat, ls, s);
+    case kF16: return launch_points_dt<kF16>(src, dst, n, P, displace, splat, ls, s);
+    case kBF16: return launch_points_dt<kBF16>(src, dst, n, P, displace, splat, ls, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys,
-                           uint32_t *rgba, const uint32_t *colors, uint32_t npx, uint32_t color,
-                           uint32_t background, const LaunchShape &ls, cudaStream_t s)
+cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
+                           const Palette &pal, uint32_t npx, const LaunchShape &ls, cudaStream_t s)
 {
     // pure streaming: one quad per thread, 256 threads, whatever the point kernel's shape
     (void)ls;
     const uint64_t quads = npx / 4;
     const int grid = (int)std::max<uint64_t>(1, (quads + 255) / 256);
-    resolve_kernel<<<grid, 256, 0, s>>>(keys, next_keys, rgba, colors, npx, color, background);
+    resolve_kernel<<<grid, 256, 0, s>>>(keys, next_keys, rgba, pal, npx);
     return cudaGetLastError();
 }
 

@@ -59,22 +59,24 @@ __device__ __forceinline__ float storage_round(float f)
 }
 
 // The ragged tail: points i0 .. n-1 of the last, partial group, with scalar
-// accesses (the vector path would read past n).
+// accesses (the vector path would read past n).  Reads src, writes dst
+// (the same buffer for an in-place step).
 template <int DT, bool kDisplace, bool kSplat>
-__device__ __forceinline__ void process_tail(void *__restrict__ pos, uint32_t n, uint32_t i0, const PointParams &P)
+__device__ __forceinline__ void process_tail(const void *src, void *dst, uint32_t n, uint32_t i0,
+                                             const PointParams &P)
 {
     for (uint32_t i = i0; i < n; ++i) {
-        float x = load_coord<DT>(pos, 3ull * i);
-        float y = load_coord<DT>(pos, 3ull * i + 1);
-        float z = load_coord<DT>(pos, 3ull * i + 2);
+        float x = load_coord<DT>(src, 3ull * i);
+        float y = load_coord<DT>(src, 3ull * i + 1);
+        float z = load_coord<DT>(src, 3ull * i + 2);
         if constexpr (kDisplace) {
             displace_point(x, y, z, i, P);
             x = storage_round<DT>(x);
             y = storage_round<DT>(y);
             z = storage_round<DT>(z);
-            store_coord<DT>(pos, 3ull * i, x);
-            store_coord<DT>(pos, 3ull * i + 1, y);
-            store_coord<DT>(pos, 3ull * i + 2, z);
+            store_coord<DT>(dst, 3ull * i, x);
+            store_coord<DT>(dst, 3ull * i + 1, y);
+            store_coord<DT>(dst, 3ull * i + 2, z);
         }
         if constexpr (kSplat) {
             uint32_t px;

@@ -1,6 +1,8 @@
 // Resolve of depth-id keys into RGBA8, shared by the single-cloud and
-// batched resolve kernels.  Empty key -> background; else colors[id] when a
-// colour buffer is bound, or the default colour.  The other depth-id buffer
+// batched resolve kernels.  Empty key -> background.  Otherwise, in order of
+// precedence: colormap[index[id]] when an index buffer is bound (an index at
+// or beyond ncolors takes the default colour), colors[id] when a per-point
+// colour buffer is bound, else the default colour.  The other depth-id buffer
 // (the one the next frame splats into) is reset to all-ones in the same pass.
 #pragma once
 
@@ -8,27 +10,37 @@
 
 namespace mmr {
 
-__device__ __forceinline__ uint32_t key_colour(unsigned long long k, const uint32_t *__restrict__ colors,
-                                               uint32_t color, uint32_t background)
+struct Palette {
+    const uint32_t *colors;    // per-point RGBA8, or null
+    const uint32_t *index;     // per-point colormap index, or null
+    const uint32_t *colormap;  // ncolors RGBA8 entries
+    uint32_t ncolors;
+    uint32_t color;            // default colour
+    uint32_t background;
+};
+
+__device__ __forceinline__ uint32_t key_colour(unsigned long long k, const Palette &pal)
 {
     if (k == kEmptyKey)
-        return background;
-    return colors ? __ldg(colors + (uint32_t)(k & 0xffffffffu)) : color;
+        return pal.background;
+    const uint32_t id = (uint32_t)(k & 0xffffffffu);
+    if (pal.index) {
+        const uint32_t c = __ldg(pal.index + id);
+        return c < pal.ncolors ? __ldg(pal.colormap + c) : pal.color;
+    }
+    return pal.colors ? __ldg(pal.colors + id) : pal.color;
 }
 
 // Four pixels starting at 4q: two 16-byte key loads, one 16-byte RGBA store,
 // two 16-byte clears.
 __device__ __forceinline__ void resolve_quad(const unsigned long long *__restrict__ keys,
                                              unsigned long long *__restrict__ next_keys,
-                                             uint32_t *__restrict__ rgba, const uint32_t *__restrict__ colors,
-                                             uint32_t q, uint32_t color, uint32_t background)
+                                             uint32_t *__restrict__ rgba, const Palette &pal, uint32_t q)
 {
     const ulonglong2 k01 = __ldcs(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q);
     const ulonglong2 k23 = __ldcs(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q + 1);
-    const uint4 c = make_uint4(key_colour(k01.x, colors, color, background),
-                               key_colour(k01.y, colors, color, background),
-                               key_colour(k23.x, colors, color, background),
-                               key_colour(k23.y, colors, color, background));
+    const uint4 c = make_uint4(key_colour(k01.x, pal), key_colour(k01.y, pal), key_colour(k23.x, pal),
+                               key_colour(k23.y, pal));
     __stcs(reinterpret_cast<uint4 *>(rgba) + q, c);
     const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
     reinterpret_cast<ulonglong2 *>(next_keys)[2 * q] = e;
@@ -37,10 +49,9 @@ __device__ __forceinline__ void resolve_quad(const unsigned long long *__restric
 
 __device__ __forceinline__ void resolve_pixel(const unsigned long long *__restrict__ keys,
                                               unsigned long long *__restrict__ next_keys,
-                                              uint32_t *__restrict__ rgba, const uint32_t *__restrict__ colors,
-                                              uint32_t p, uint32_t color, uint32_t background)
+                                              uint32_t *__restrict__ rgba, const Palette &pal, uint32_t p)
 {
-    rgba[p] = key_colour(keys[p], colors, color, background);
+    rgba[p] = key_colour(keys[p], pal);
     next_keys[p] = kEmptyKey;
 }
 

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) serve_private_kernel(ServeTables T)
                 process_words<DT, true, true>(q, g * G, G, P);
                 store_words(vw.pos, g, q);
             } else {
-                process_tail<DT, true, true>(vw.pos, n, g * G, P);
+                process_tail<DT, true, true>(vw.pos, vw.pos, n, g * G, P);
             }
         }
     }

@@ -126,7 +126,7 @@ extern "C" mmr_status mmr_render_static(const void *dev_points, uint64_t n, int 
         LaunchShape ls;
         ls.sm_count = sms;
         // render only: the point buffer is read, never written
-        e = launch_points(dtype, const_cast<void *>(dev_points), (uint32_t)n, P, false, true, ls, s);
+        e = launch_points(dtype, dev_points, nullptr, (uint32_t)n, P, false, true, ls, s);
     }
     if (e == cudaSuccess) {
         static_resolve_kernel<<<grid_px, 256, 0, s>>>(keys, dev_rgba, npx, color, background);

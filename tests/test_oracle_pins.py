@@ -383,3 +383,58 @@ def test_inputs_module_encoding_agrees_with_oracle_conversions():
         assert np.array_equal(inputs.encode(pos64, fmt), oracle.to_storage(p32, fmt))
         assert np.array_equal(inputs.decode(inputs.encode(pos64, fmt), fmt),
                               oracle.from_storage(inputs.encode(pos64, fmt), fmt))
+
+
+# --------------------------------------------------------------------------
+# Disc markers: brute-force per-pixel search and lattice-point counts.
+# --------------------------------------------------------------------------
+def _brute_force_disc(pos32, M32, W, H, radius):
+    """Independent restatement: for every pixel, every point; numpy float32
+    arithmetic (IEEE round-to-nearest) in the stated order."""
+    f = np.float32
+    M = M32.astype(np.float32)
+    x, y, z = pos32[:, 0], pos32[:, 1], pos32[:, 2]
+    cx = ((M[0, 0] * x + M[0, 1] * y) + M[0, 2] * z) + M[0, 3]
+    cy = ((M[1, 0] * x + M[1, 1] * y) + M[1, 2] * z) + M[1, 3]
+    cw = ((M[3, 0] * x + M[3, 1] * y) + M[3, 2] * z) + M[3, 3]
+    ok = (cw > f(0.1)) & (cw < f(100.0))
+    with np.errstate(all="ignore"):
+        sx = (cx / cw + f(1.0)) * f(0.5 * W)
+        sy = (f(1.0) - cy / cw) * f(0.5 * H)
+    r2 = f(radius) * f(radius)
+    keys = (cw.view(np.uint32).astype(np.uint64) << np.uint64(32)) | np.arange(len(x), dtype=np.uint64)
+    want = np.full(W * H, 0xFFFFFFFFFFFFFFFF, np.uint64)
+    for py in range(H):
+        dy = (f(py) + f(0.5)) - sy
+        for px in range(W):
+            dx = (f(px) + f(0.5)) - sx
+            cov = ok & ((dx * dx + dy * dy) <= r2)
+            if cov.any():
+                want[py * W + px] = keys[cov].min()
+    return want
+
+
+@pytest.mark.parametrize("radius", [0.5, 1.0, 2.5, 4.0])
+def test_disc_splat_matches_brute_force(radius):
+    W, H = 40, 30
+    pos = inputs.encode(inputs.gaussian_mixture_cloud(600, 40, components=3, sigma=0.08), "f32")
+    M = oracle.camera_f32(EYE, CEN, UP, 60.0, W / H, 0.1, 100.0)
+    keys = oracle.empty_keys(W, H)
+    oracle.splat_disc(pos, M, W, H, 0.1, 100.0, radius, keys)
+    assert np.array_equal(keys, _brute_force_disc(pos, M, W, H, radius))
+
+
+@pytest.mark.parametrize("radius,count", [(1.0, 5), (2.0, 13), (3.0, 29), (0.5, 1)])
+def test_disc_covers_lattice_points_of_circle(radius, count):
+    """A point projected exactly onto a pixel centre covers the pixels whose
+    centres are within r: the number of integer lattice points in a disc of
+    radius r (Gauss circle problem: 5, 13, 29 for r = 1, 2, 3)."""
+    W = H = 21
+    # plain matrix: sx = (x/z + 1) W/2 with z = w = 1; x chosen so that sx = 10.5 (centre of pixel 10)
+    M = np.zeros((4, 4), np.float32)
+    M[0, 0] = M[1, 1] = M[3, 2] = 1.0
+    xc = np.float32(10.5 / (W / 2) - 1.0)
+    pos = np.array([[xc, -xc, 1.0]], np.float32)
+    keys = oracle.empty_keys(W, H)
+    oracle.splat_disc(pos, M, W, H, 0.1, 100.0, radius, keys)
+    assert int((keys != oracle.EMPTY_KEY).sum()) == count

@@ -152,3 +152,102 @@ def test_single_pixel_framebuffer_and_tall_frame():
     for W, H in [(1, 1), (1, 1000), (999, 1)]:
         args = (stored, "f32", W, H, 2, 1e-3, 2, fixed_eye)
         _assert_same(gpu_run(*args), oracle_run(*args), f"{W}x{H}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_pingpong_matches_in_place_and_keeps_previous_state(dtype):
+    """Out-of-place stepping into the other buffer (the paper's alternating
+    buffers): same positions and frames as the oracle's in-place steps, and
+    the buffer that was read still holds the previous state."""
+    from paper_2504_20937_b300.api import Context
+    n, W, H, frames, seed, a = 40_003, 120, 90, 5, 13, 1e-3
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 28, components=3, sigma=0.05), dtype)
+    eye = orbit(4.0)
+    tview = np.float32 if dtype == "f32" else np.int16
+    with Context(W, H) as ctx:
+        bufs = ctx.alloc_pingpong(n, dtype)
+        bufs[0].copy_(torch.from_numpy(stored.view(tview)))
+        ctx.set_sim(seed, 0, a, 0)
+        for f in range(frames):
+            before = ctx.points.clone()
+            read = ctx.visible
+            ctx.set_camera(eye(f), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)
+            ctx.step_and_render_pingpong()
+            torch.cuda.synchronize()
+            assert ctx.visible == 1 - read
+            assert torch.equal(bufs[read], before)            # the state that was read is untouched
+        gpos = ctx.points.cpu().numpy().view(stored.dtype)
+        gkeys = ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64)
+        grgba = ctx.frame_rgba().cpu().numpy().reshape(-1).view(np.uint32)
+        # rendering the other (previous) buffer gives the previous state's frame
+        ctx.set_visible(1 - ctx.visible)
+        ctx.render()
+        torch.cuda.synchronize()
+        prev_keys = ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64)
+    o = oracle_run(stored, dtype, W, H, seed, a, frames, eye)
+    assert np.array_equal(gpos.view(np.uint8), o[0].view(np.uint8))
+    assert np.array_equal(gkeys, o[1]) and np.array_equal(grgba, o[2])
+    prev = oracle_run(stored, dtype, W, H, seed, a, frames - 1, eye)[0]
+    M = oracle.camera_f32(eye(frames - 1), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, W / H, 0.1, 100.0)
+    want_prev, _ = oracle.render(prev, dtype, M, W, H, np.float32(0.1), np.float32(100.0))
+    assert np.array_equal(prev_keys, want_prev)
+
+
+def test_indexed_colours():
+    """colour = colormap[index[id]] (index >= ncolors takes the default)."""
+    from paper_2504_20937_b300.api import Context
+    n, W, H, ncolors = 25_000, 100, 80, 9
+    stored = inputs.encode(inputs.uniform_cloud(n, 29), "f32")
+    rng = np.random.default_rng(3)
+    index = rng.integers(0, ncolors + 2, size=n).astype(np.uint32)
+    cmap = rng.integers(0, 2**32, size=ncolors, dtype=np.uint64).astype(np.uint32)
+    default = 0xFF112233
+    with Context(W, H) as ctx:
+        ctx.alloc_points(n, "f32").copy_(torch.from_numpy(stored))
+        idx, cm = ctx.alloc_indexed_colors(ncolors)
+        idx.copy_(torch.from_numpy(index.view(np.int32)))
+        cm.copy_(torch.from_numpy(cmap.view(np.int32)))
+        ctx.set_sim(5, 0, 1e-3, 0)
+        ctx.set_style(default, 0x44)
+        for f in range(2):
+            ctx.set_camera(fixed_eye(f), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)
+            ctx.step_and_render()
+        torch.cuda.synchronize()
+        grgba = ctx.frame_rgba().cpu().numpy().reshape(-1).view(np.uint32)
+    per_point = np.where(index < ncolors, cmap[np.minimum(index, ncolors - 1)], default).astype(np.uint32)
+    o = oracle_run(stored, "f32", W, H, 5, 1e-3, 2, fixed_eye, colors=per_point, color=default, background=0x44)
+    assert np.array_equal(grgba, o[2])
+    assert len(np.unique(grgba)) > ncolors // 2
+
+
+@pytest.mark.parametrize("dtype,radius", [("f32", 0.5), ("f32", 1.0), ("f32", 2.5), ("f32", 4.0), ("f16", 2.0),
+                                          ("bf16", 1.5)])
+def test_disc_markers_bit_exact(dtype, radius):
+    """Disc markers of radius r pixels against the oracle (ragged n, odd
+    frame, clustered cloud so discs overlap heavily)."""
+    from paper_2504_20937_b300.api import Context
+    n, W, H, frames, seed, a = 20_003, 97, 61, 2, 17, 1e-3
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 30, components=3, sigma=0.05), dtype)
+    eye = orbit(6.0)
+    tview = np.float32 if dtype == "f32" else np.int16
+    with Context(W, H) as ctx:
+        ctx.alloc_points(n, dtype).copy_(torch.from_numpy(stored.view(tview)))
+        ctx.set_sim(seed, 0, a, 0)
+        ctx.set_marker(radius)
+        for f in range(frames):
+            ctx.set_camera(eye(f), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)
+            ctx.step_and_render()
+        torch.cuda.synchronize()
+        gpos = ctx.points.cpu().numpy().view(stored.dtype)
+        gkeys = ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64)
+        grgba = ctx.frame_rgba().cpu().numpy().reshape(-1).view(np.uint32)
+    pos = stored.copy()
+    for f in range(frames):
+        oracle.displace(pos, dtype, seed, 0, f, np.float32(a))
+    M = oracle.camera_f32(eye(frames - 1), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, W / H, 0.1, 100.0)
+    keys, rgba = oracle.render_disc(oracle.from_storage(pos, dtype), M, W, H, np.float32(0.1), np.float32(100.0),
+                                    np.float32(radius))
+    assert np.array_equal(gpos.view(np.uint8), pos.view(np.uint8))
+    assert np.array_equal(gkeys, keys), f"{np.count_nonzero(gkeys != keys)} pixels differ"
+    assert np.array_equal(grgba, rgba)
+    assert (gkeys != oracle.EMPTY_KEY).sum() > 100          # the discs are really drawn
