@@ -327,6 +327,7 @@ def run_ours(args, rank, world, local):
         ctx.close()
         out["c3_64Mpts_gmm16_3840x2160"] = run_c3(make_ctx, timed_frames, hbm_gbs)
         out["features_c2"] = run_features(sc, stored, hbm_gbs)
+        out["nbody"] = run_nbody()
         out["batched_256_clouds"] = run_batched(hbm_gbs)
         out["served"] = run_served()
     else:
@@ -408,6 +409,37 @@ def run_features(sc, stored, hbm_gbs, frames=50):
             step = (lambda c: c.step_and_render_pingpong(stream)) if pingpong else (lambda c: c.step_and_render(stream))
             res[name] = time_frames(ctx, step)
     return res
+
+
+def run_nbody(sizes=(16384, 65536), steps=10):
+    """Second workload: all-pairs gravity feeding the renderer (1920x1080),
+    one fused step+splat kernel plus resolve per frame.  Compute-bound: the
+    roofline is the FP32 issue rate (no FMA contraction on this path), here
+    counted as 20 FP32 operations per interaction (sqrt and divide as one
+    each) against 148 SMs x 128 lanes x the measured SM clock."""
+    import torch
+    from paper_2504_20937_b300.api import Context
+    out = {}
+    stream = torch.cuda.current_stream()
+    for n in sizes:
+        pos = inputs.encode(inputs.gaussian_mixture_cloud(n, 70, components=4, sigma=0.05), "f32")
+        with Context(1920, 1080) as ctx:
+            ctx.alloc_pingpong(n, "f32")[0].copy_(torch.from_numpy(pos))
+            v, m = ctx.alloc_nbody()
+            m.fill_(1.0 / n)
+            ctx.set_timing(True)
+            ms = []
+            for f in range(steps + 2):
+                ctx.set_camera(inputs.orbit_eye(f, 0.36), CENTRE, UP, 60.0, 0.1, 100.0)
+                ctx.nbody_step_and_render(1e-3, 1e-4, 1e-3, stream)
+                pk, rk = ctx.last_kernel_ms()
+                if f >= 2:
+                    ms.append(pk)
+        k = statistics.mean(ms)
+        inter = float(n) * n
+        out[f"n{n}"] = {"nbody_kernel_ms": k, "interactions_per_s": inter / (k / 1e3),
+                        "gflops_20_per_interaction": 20 * inter / (k / 1e3) / 1e9}
+    return out
 
 
 def run_batched(hbm_gbs, frames=100):

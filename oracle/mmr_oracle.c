@@ -460,6 +460,62 @@ void orc_splat_disc_f32(const float *pos, uint64_t n, const float M[16], int W, 
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Second workload: gravitational all-pairs N-body (the paper's N-body       */
+/* sample, Sec. 4.2.3), written from the physics.  Softened Newtonian        */
+/* gravity, for body i summed over j = 0 .. n-1 in order (the j = i term is  */
+/* zero):  d = p_j - p_i,  r2 = ((dx dx + dy dy) + dz dz) + eps2,            */
+/*         inv = 1 / sqrt(r2),  s = m_j ((inv inv) inv),  acc += d s;        */
+/* then a = G acc, v' = v + a dt, p' = p + v' dt (semi-implicit Euler).      */
+/* FP32, every operation rounded once, in that order; positions are read    */
+/* from pin and written to pout (two buffers, as the paper's ping-pong).     */
+/* ------------------------------------------------------------------------ */
+void orc_nbody_step_f32(const float *pin, float *pout, float *vel, const float *mass, uint64_t n, float G,
+                        float eps2, float dt)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        const float px = pin[3 * i], py = pin[3 * i + 1], pz = pin[3 * i + 2];
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        for (uint64_t j = 0; j < n; ++j) {
+            float dx = pin[3 * j] - px;
+            float dy = pin[3 * j + 1] - py;
+            float dz = pin[3 * j + 2] - pz;
+            float r2 = ((dx * dx + dy * dy) + dz * dz) + eps2;
+            float inv = 1.0f / sqrtf(r2);
+            float s = mass[j] * ((inv * inv) * inv);
+            ax = ax + dx * s;
+            ay = ay + dy * s;
+            az = az + dz * s;
+        }
+        float vx = vel[3 * i] + (G * ax) * dt;
+        float vy = vel[3 * i + 1] + (G * ay) * dt;
+        float vz = vel[3 * i + 2] + (G * az) * dt;
+        vel[3 * i] = vx;
+        vel[3 * i + 1] = vy;
+        vel[3 * i + 2] = vz;
+        pout[3 * i] = px + vx * dt;
+        pout[3 * i + 1] = py + vy * dt;
+        pout[3 * i + 2] = pz + vz * dt;
+    }
+}
+
+/* FP64 accelerations G * sum_j m_j d / (|d|^2 + eps2)^(3/2), for the pins. */
+void orc_nbody_accel_f64(const double *p, const double *mass, uint64_t n, double G, double eps2, double *acc)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        double a[3] = { 0.0, 0.0, 0.0 };
+        for (uint64_t j = 0; j < n; ++j) {
+            double d[3] = { p[3 * j] - p[3 * i], p[3 * j + 1] - p[3 * i + 1], p[3 * j + 2] - p[3 * i + 2] };
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+            double s = mass[j] / (r2 * sqrt(r2));
+            for (int k = 0; k < 3; ++k)
+                a[k] += d[k] * s;
+        }
+        for (int k = 0; k < 3; ++k)
+            acc[3 * i + k] = G * a[k];
+    }
+}
+
 /* Resolve: key -> RGBA8.  colors == NULL means every point takes `color`. */
 void orc_resolve(const uint64_t *keybuf, uint64_t npx, const uint32_t *colors, uint32_t color,
                  uint32_t background, uint32_t *rgba)

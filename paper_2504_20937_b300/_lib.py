@@ -41,6 +41,8 @@ SIGNATURES = {
     "mmr_get_visible": (_i, [_vp, C.POINTER(_i)]),
     "mmr_step_and_render_pingpong": (_i, [_vp, _vp]),
     "mmr_alloc_indexed_colors": (_i, [_vp, _u32, C.POINTER(_vp), C.POINTER(_vp)]),
+    "mmr_alloc_nbody": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
+    "mmr_nbody_step_and_render": (_i, [_vp, _f, _f, _f, _vp]),
     "mmr_set_camera": (_i, [_vp, _d3, _d3, _d3, _d, _d, _d]),
     "mmr_set_matrix": (_i, [_vp, _f16, _f, _f]),
     "mmr_get_matrix": (_i, [_vp, _f16]),

@@ -102,6 +102,16 @@ class Context:
     def step_and_render_pingpong(self, stream=None):
         self._check(self._lib.mmr_step_and_render_pingpong(self._h, stream_handle(stream)))
 
+    def alloc_nbody(self):
+        """(velocities float32[n,3] view, masses float32[n] view) for the
+        N-body workload (needs FP32 ping-pong buffers)."""
+        v, m = C.c_void_p(), C.c_void_p()
+        self._check(self._lib.mmr_alloc_nbody(self._h, C.byref(v), C.byref(m)))
+        return device_view(v.value, (self.n, 3), "<f4"), device_view(m.value, (self.n,), "<f4")
+
+    def nbody_step_and_render(self, G: float, eps2: float, dt: float, stream=None):
+        self._check(self._lib.mmr_nbody_step_and_render(self._h, G, eps2, dt, stream_handle(stream)))
+
     def alloc_indexed_colors(self, ncolors: int):
         """(index int32[n] view, colormap int32[ncolors] view)."""
         i, m = C.c_void_p(), C.c_void_p()

@@ -38,6 +38,8 @@ struct mmr_ctx {
     int dtype = 0;
     uint64_t point_bytes = 0;
     uint32_t *colors = nullptr;
+    float *nb_vel = nullptr;             // N-body workload: velocities (3n) and masses (n)
+    float *nb_mass = nullptr;
     uint32_t *index = nullptr;           // indexed colour: colormap[index[id]]
     uint32_t *colormap = nullptr;
     uint32_t ncolors = 0;
@@ -358,6 +360,8 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     dev_free(ctx, &ctx->buf[1], storage_bytes(ctx->n, ctx->dtype));
     dev_free(ctx, (void **)&ctx->colors, ctx->n * 4);
     dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
+    dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
+    dev_free(ctx, (void **)&ctx->nb_mass, ctx->n * 4);
     dev_free(ctx, (void **)&ctx->colormap, (uint64_t)ctx->ncolors * 4);
     dev_free(ctx, &ctx->rt_device, storage_bytes(ctx->n, ctx->dtype));
     if (ctx->rt_host) {
@@ -460,6 +464,74 @@ mmr_status mmr_step_and_render_pingpong(mmr_ctx *ctx, void *stream)
     return st;
 }
 
+mmr_status mmr_alloc_nbody(mmr_ctx *ctx, float **dev_vel, float **dev_mass)
+{
+    if (!ctx || !dev_vel || !dev_mass)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_alloc_nbody: NULL argument");
+    *dev_vel = nullptr;
+    *dev_mass = nullptr;
+    if (!ctx->buf[1] || ctx->dtype != MMR_F32x3)
+        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_nbody: needs FP32 ping-pong buffers (mmr_alloc_pingpong)");
+    if (ctx->nb_vel)
+        return fail(ctx, MMR_ERR_STATE, "mmr_alloc_nbody: already allocated");
+    mmr_status st = dev_alloc(ctx, (void **)&ctx->nb_vel, ctx->n * 12, "N-body velocities");
+    if (st == MMR_OK)
+        st = dev_alloc(ctx, (void **)&ctx->nb_mass, ctx->n * 4, "N-body masses");
+    if (st != MMR_OK) {
+        dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
+        return st;
+    }
+    cudaError_t e = cudaMemset(ctx->nb_vel, 0, ctx->n * 12);
+    if (e == cudaSuccess)
+        e = cudaMemset(ctx->nb_mass, 0, ctx->n * 4);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_alloc_nbody: clearing");
+    *dev_vel = ctx->nb_vel;
+    *dev_mass = ctx->nb_mass;
+    return MMR_OK;
+}
+
+mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt, void *stream)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = check_frame_ready(ctx, true);
+    if (st != MMR_OK)
+        return st;
+    if (!ctx->nb_vel)
+        return fail(ctx, MMR_ERR_STATE, "mmr_nbody_step_and_render: call mmr_alloc_nbody first");
+    if (!std::isfinite(G) || !(eps2 > 0.0f) || !std::isfinite(eps2) || !std::isfinite(dt))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_nbody_step_and_render: need finite G, dt and eps2 > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    mmr::PointParams P = point_params(ctx);
+    const mmr::NbodyParams B{G, eps2, dt};
+    const int r = ctx->visible;
+    if (ctx->timing)
+        cudaEventRecord(ctx->ev[0], s);
+    cudaError_t e = mmr::launch_nbody(static_cast<const float *>(ctx->buf[r]), static_cast<float *>(ctx->buf[r ^ 1]),
+                                      ctx->nb_vel, ctx->nb_mass, (uint32_t)ctx->n, B, P, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "N-body kernel launch");
+    if (ctx->timing)
+        cudaEventRecord(ctx->ev[1], s);
+    const int cur = ctx->splat_buf;
+    e = mmr::launch_resolve(ctx->keys[cur], ctx->keys[cur ^ 1], ctx->rgba, palette(ctx), (uint32_t)frame_px(ctx),
+                            ctx->launch, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "resolve kernel launch");
+    if (ctx->timing) {
+        cudaEventRecord(ctx->ev[2], s);
+        ctx->timed_frame = true;
+    }
+    ctx->latest_buf = cur;
+    ctx->splat_buf = cur ^ 1;
+    ctx->visible = r ^ 1;
+    ctx->step += 1;
+    return MMR_OK;
+}
+
 mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint32_t **dev_index, uint32_t **dev_colormap)
 {
     if (!ctx || !dev_index || !dev_colormap || ncolors == 0 || ncolors > (1u << 24))
@@ -475,6 +547,8 @@ mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint32_t **d
         st = dev_alloc(ctx, (void **)&ctx->colormap, (uint64_t)ncolors * 4, "colormap");
     if (st != MMR_OK) {
         dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
+    dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
+    dev_free(ctx, (void **)&ctx->nb_mass, ctx->n * 4);
         return st;
     }
     ctx->ncolors = ncolors;

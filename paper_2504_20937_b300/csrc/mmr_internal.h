@@ -41,6 +41,18 @@ cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *n
 // Message returned by mmr_last_error(NULL) on this thread.
 void set_process_error(const char *msg);
 
+// All-pairs gravity step parameters.
+struct NbodyParams {
+    float G;
+    float eps2;
+    float dt;
+};
+
+// One N-body step reading pin, writing pout and vel, splatting the new
+// positions into P.keys (FP32 positions, n bodies).
+cudaError_t launch_nbody(const float *pin, float *pout, float *vel, const float *mass, uint32_t n,
+                         const NbodyParams &B, const PointParams &P, cudaStream_t s);
+
 // FP64 camera -> FP32 clip matrix (row-major 4x4); returns false on invalid input.
 bool build_clip_matrix(const double eye[3], const double target[3], const double up[3],
                        double fovy_deg, double aspect, double znear, double zfar, float out[16]);

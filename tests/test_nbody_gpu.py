@@ -1,0 +1,66 @@
+"""Second workload: gravitational all-pairs N-body feeding the renderer,
+bit-exact against the oracle (positions, velocities, keys, RGBA)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2504_20937_b300 import inputs
+from paper_2504_20937_b300.api import Context, MmrError
+
+pytestmark = pytest.mark.gpu
+
+CEN = (0.5, 0.5, 0.5)
+UP = (0.0, 1.0, 0.0)
+
+
+@pytest.mark.parametrize("n", [1, 255, 257, 3001])
+def test_nbody_steps_bit_exact(n):
+    W, H, steps = 96, 64, 3
+    G, eps2, dt = np.float32(2e-4), np.float32(1e-3), np.float32(5e-2)
+    pos = inputs.encode(inputs.gaussian_mixture_cloud(n, 60 + n, components=2, sigma=0.08), "f32")
+    mass = np.random.default_rng(n).uniform(0.5, 2.0, n).astype(np.float32)
+    vel0 = (np.random.default_rng(n + 1).standard_normal((n, 3)) * 0.01).astype(np.float32)
+    eye = lambda f: inputs.orbit_eye(f, 3.0)  # noqa: E731
+    with Context(W, H) as ctx:
+        bufs = ctx.alloc_pingpong(n, "f32")
+        bufs[0].copy_(torch.from_numpy(pos))
+        v, m = ctx.alloc_nbody()
+        v.copy_(torch.from_numpy(vel0))
+        m.copy_(torch.from_numpy(mass))
+        for f in range(steps):
+            ctx.set_camera(eye(f), CEN, UP, 60.0, 0.1, 100.0)
+            ctx.nbody_step_and_render(float(G), float(eps2), float(dt))
+        torch.cuda.synchronize()
+        gpos = ctx.points.cpu().numpy()
+        gvel = v.cpu().numpy()
+        gkeys = ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64)
+        grgba = ctx.frame_rgba().cpu().numpy().reshape(-1).view(np.uint32)
+        assert ctx.visible == steps % 2
+    p, vel = pos.copy(), vel0.copy()
+    for f in range(steps):
+        p = oracle.nbody_step_f32(p, vel, mass, G, eps2, dt)
+    M = oracle.camera_f32(eye(steps - 1), CEN, UP, 60.0, W / H, 0.1, 100.0)
+    keys, rgba = oracle.render(p, "f32", M, W, H, np.float32(0.1), np.float32(100.0))
+    assert np.array_equal(gpos, p)
+    assert np.array_equal(gvel, vel)
+    assert np.array_equal(gkeys, keys) and np.array_equal(grgba, rgba)
+    if n > 1:
+        assert not np.array_equal(gpos, pos)           # the bodies did move
+
+
+def test_nbody_needs_fp32_pingpong():
+    with Context(16, 16) as ctx:
+        ctx.alloc_points(10, "f32")
+        with pytest.raises(MmrError, match="STATE"):
+            ctx.alloc_nbody()
+    with Context(16, 16) as ctx:
+        ctx.alloc_pingpong(10, "f16")
+        with pytest.raises(MmrError, match="STATE"):
+            ctx.alloc_nbody()
+    with Context(16, 16) as ctx:
+        ctx.alloc_pingpong(10, "f32")
+        ctx.alloc_nbody()
+        ctx.set_camera((0.5, 0.5, 2.5), CEN, UP, 60.0, 0.1, 100.0)
+        with pytest.raises(MmrError, match="INVALID"):
+            ctx.nbody_step_and_render(1.0, 0.0, 0.01)     # eps2 must be > 0

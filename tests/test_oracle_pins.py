@@ -438,3 +438,41 @@ def test_disc_covers_lattice_points_of_circle(radius, count):
     keys = oracle.empty_keys(W, H)
     oracle.splat_disc(pos, M, W, H, 0.1, 100.0, radius, keys)
     assert int((keys != oracle.EMPTY_KEY).sum()) == count
+
+
+# --------------------------------------------------------------------------
+# N-body (second workload): two-body closed form, brute force, conservation.
+# --------------------------------------------------------------------------
+def test_nbody_two_body_closed_form():
+    """Two bodies of mass m at rest, distance d apart on x: each is pulled
+    towards the other with a = G m d / (d^2 + eps2)^(3/2)."""
+    G, m, d, eps2, dt = 1.0, 2.0, 0.5, 1e-4, 1e-3
+    pos = np.array([[0.0, 0.0, 0.0], [d, 0.0, 0.0]], np.float32)
+    vel = np.zeros_like(pos)
+    out = oracle.nbody_step_f32(pos, vel, np.array([m, m], np.float32), np.float32(G), np.float32(eps2),
+                                np.float32(dt))
+    a = G * m * d / (d * d + eps2) ** 1.5
+    assert vel[0, 0] == pytest.approx(a * dt, rel=1e-6) and vel[1, 0] == pytest.approx(-a * dt, rel=1e-6)
+    assert np.all(vel[:, 1:] == 0)
+    assert out[0, 0] == pytest.approx(a * dt * dt, rel=1e-5) and out[1, 0] == pytest.approx(d - a * dt * dt, rel=1e-6)
+
+
+def test_nbody_matches_fp64_brute_force_and_conserves_momentum():
+    n = 300
+    rng = np.random.default_rng(8)
+    pos = inputs.encode(inputs.gaussian_mixture_cloud(n, 41, components=2, sigma=0.1), "f32")
+    mass = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    G, eps2, dt = np.float32(1e-3), np.float32(1e-3), np.float32(1e-2)
+    vel = np.zeros_like(pos)
+    oracle.nbody_step_f32(pos, vel, mass, G, eps2, dt)
+    acc64 = oracle.nbody_accel_f64(pos.astype(np.float64), mass.astype(np.float64), float(G), float(eps2))
+    # independent numpy restatement in float64
+    d = pos.astype(np.float64)[None, :, :] - pos.astype(np.float64)[:, None, :]
+    r2 = (d ** 2).sum(-1) + float(eps2)
+    acc_np = float(G) * (d * (mass.astype(np.float64)[None, :] / r2 ** 1.5)[..., None]).sum(1)
+    assert np.allclose(acc64, acc_np, rtol=1e-12, atol=1e-15)
+    assert np.allclose(vel / float(dt), acc64, rtol=2e-4, atol=1e-6)
+    # pairwise forces cancel: total momentum stays at zero up to FP32 rounding
+    p_tot = (mass[:, None].astype(np.float64) * vel.astype(np.float64)).sum(0)
+    scale = (mass[:, None] * np.abs(vel)).sum(0)
+    assert np.all(np.abs(p_tot) <= 1e-4 * scale)
