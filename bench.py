@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "pr1"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "pr1", "c3"])
     ap.add_argument("--no-extra", action="store_true", help="skip the 64M-point and round-trip legs")
     ap.add_argument("--cpu-frames", type=int, default=60, help="oracle frames for the CPU baseline (0: skip)")
     ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
@@ -70,7 +70,7 @@ def dist_env():
 
 def scene_for(name, points=0):
     import dataclasses
-    sc = inputs.C2 if name == "c2" else inputs.PR1
+    sc = {"c2": inputs.C2, "pr1": inputs.PR1, "c3": inputs.C3}[name]
     if points:
         sc = dataclasses.replace(sc, n=points, name=f"{sc.name}_n{points}")
     return sc
