@@ -86,6 +86,71 @@ def _to_torch(stored: np.ndarray) -> torch.Tensor:
     return torch.from_numpy(stored if stored.dtype == np.float32 else stored.view(np.int16))
 
 
+class ContinuousBatcher:
+    """The scheduling policy of the request loop, free of any device work.
+
+    Viewers arrive (`arrive`), wait in FIFO order, and are admitted while a
+    slot is free and the engine accepts them (`admit` asks a callback, which
+    returns None when the engine's memory budget refuses the viewer: the
+    queue then stops, so arrival order is kept).  Every tick renders one frame
+    for each admitted viewer (`tick_done`), which records each frame's
+    latency from its request time and retires viewers whose last frame is
+    done.
+    """
+
+    def __init__(self, max_viewers: int):
+        self.max_viewers = max_viewers
+        self.pending = collections.deque()
+        self.waiting = collections.deque()
+        self.active = {}              # engine id -> [request, frames done, request time]
+        self.refused = 0
+
+    def load(self, trace):
+        self.pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
+
+    def arrive(self, now: float) -> None:
+        while self.pending and self.pending[0].arrival_s <= now:
+            self.waiting.append(self.pending.popleft())
+
+    def admit(self, try_add) -> list:
+        """try_add(request) -> engine id or None; returns the admitted (id, request)."""
+        admitted = []
+        while self.waiting and len(self.active) < self.max_viewers:
+            req = self.waiting[0]
+            vid = try_add(req)
+            if vid is None:
+                self.refused += 1
+                break
+            self.waiting.popleft()
+            self.active[vid] = [req, 0, req.arrival_s]
+            admitted.append((vid, req))
+        return admitted
+
+    def frames_due(self):
+        """(engine id, request, frame index) of every frame the next tick renders."""
+        return [(vid, st[0], st[1]) for vid, st in self.active.items()]
+
+    def tick_done(self, done: float):
+        """Account one tick finished at time `done`; returns (latencies of
+        first frames, latencies of later frames, retired engine ids)."""
+        first, later, finished = [], [], []
+        for vid, st in self.active.items():
+            req, k, req_time = st
+            (first if k == 0 else later).append(done - req_time)
+            st[1], st[2] = k + 1, done
+            if st[1] >= req.frames:
+                finished.append(vid)
+        for vid in finished:
+            del self.active[vid]
+        return first, later, finished
+
+    def busy(self) -> bool:
+        return bool(self.pending or self.waiting or self.active)
+
+    def next_arrival(self):
+        return self.pending[0].arrival_s if self.pending else None
+
+
 def run_trace(trace, cfg: ServeConfig, roundtrip: bool = False, clouds=None, shared=None) -> ServeStats:
     """Serve every request of `trace`; returns the statistics.
 
@@ -99,55 +164,46 @@ def run_trace(trace, cfg: ServeConfig, roundtrip: bool = False, clouds=None, sha
     host_clouds = {v: _to_torch(c).pin_memory() for v, c in clouds.items()}
     stats = ServeStats()
     stream = torch.cuda.current_stream()
+    sched = ContinuousBatcher(cfg.max_viewers)
+    sched.load(trace)
     with Server(cfg.shared_n, cfg.dtype, cfg.shared_seed, 0, cfg.amplitude, cfg.budget_bytes) as srv:
         srv.shared_points().copy_(_to_torch(shared))
         srv.set_shared_color(cfg.shared_color)
         srv.set_timing(True)
         torch.cuda.synchronize()
-        pending = collections.deque(sorted(trace, key=lambda r: r.arrival_s))
-        waiting = collections.deque()
-        active = {}                     # engine viewer id -> [request, frames done, request time]
+
+        def try_add(req):
+            return srv.try_add_viewer(req.private_n, req.W, req.H, seed=req.init_seed, cloud=1 + req.viewer,
+                                      amplitude=cfg.amplitude, color=0xFF000000 | (req.viewer & 0xFFFFFF))
+
         t0 = time.perf_counter()
-        while pending or waiting or active:
+        while sched.busy():
             now = time.perf_counter() - t0
-            while pending and pending[0].arrival_s <= now:
-                waiting.append(pending.popleft())
-            while waiting and len(active) < cfg.max_viewers:
-                req = waiting[0]
-                vid = srv.try_add_viewer(req.private_n, req.W, req.H, seed=req.init_seed, cloud=1 + req.viewer,
-                                         amplitude=cfg.amplitude, color=0xFF000000 | (req.viewer & 0xFFFFFF))
-                if vid is None:
-                    stats.refused_for_budget += 1
-                    break
-                waiting.popleft()
+            sched.arrive(now)
+            for vid, req in sched.admit(try_add):
                 srv.viewer_points(vid).copy_(host_clouds[req.viewer], non_blocking=True)
                 stats.queue_wait_ms.append(1e3 * max(0.0, (time.perf_counter() - t0) - req.arrival_s))
-                active[vid] = [req, 0, req.arrival_s]
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, min(pending[0].arrival_s - now, 0.001)))
+            due = sched.frames_due()
+            if not due:
+                nxt = sched.next_arrival()
+                if nxt is not None:
+                    time.sleep(max(0.0, min(nxt - now, 0.001)))
                 continue
-            stats.max_active = max(stats.max_active, len(active))
-            stats.active_per_tick.append(len(active))
-            for vid, (req, k, _) in active.items():
+            stats.max_active = max(stats.max_active, len(due))
+            stats.active_per_tick.append(len(due))
+            for vid, req, k in due:
                 srv.set_camera(vid, viewer_eye(req, k, cfg), CENTRE, UP, cfg.fovy_deg, cfg.znear, cfg.zfar)
             srv.tick(stream, roundtrip=roundtrip)
             stats.tick_ms.append(srv.last_tick_ms())      # waits for the tick
             done = time.perf_counter() - t0
             stats.ticks += 1
-            finished = []
-            for vid, st in active.items():
-                req, k, req_time = st
-                stats.latencies_ms.append(1e3 * (done - req_time))
-                if k > 0:
-                    stats.steady_latencies_ms.append(1e3 * (done - req_time))
-                stats.frames += 1
-                stats.points_rendered += cfg.shared_n + req.private_n
-                st[1], st[2] = k + 1, done
-                if st[1] >= req.frames:
-                    finished.append(vid)
+            first, later, finished = sched.tick_done(done)
+            stats.latencies_ms += [1e3 * x for x in first + later]
+            stats.steady_latencies_ms += [1e3 * x for x in later]
+            stats.frames += len(due)
+            stats.points_rendered += sum(cfg.shared_n + req.private_n for _, req, _ in due)
             for vid in finished:
                 srv.remove_viewer(vid)
-                del active[vid]
+        stats.refused_for_budget = sched.refused
         stats.wall_s = time.perf_counter() - t0
     return stats
