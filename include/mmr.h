@@ -185,10 +185,12 @@ MMR_API mmr_status mmr_step_and_render_pingpong(mmr_ctx *ctx, void *stream);
  * sample, Sec. 4.2.3) feeding the same renderer.  mmr_alloc_nbody needs FP32
  * ping-pong buffers (the visible one holds the bodies' positions) and
  * allocates velocities (3n floats, zero) and masses (n floats, zero; write
- * them) and returns their device pointers.  mmr_nbody_step_and_render: for
- * every body i, acc = sum over j = 0..n-1 in order of (p_j - p_i) m_j /
- * (|p_j - p_i|^2 + eps2)^(3/2) (FP32, exact sqrt and division, fixed order),
- * v += G acc dt, p' = p + v dt written to the other buffer, which is then
+ * them), plus scratch for per-chunk sums, and returns the velocity and mass
+ * device pointers.  mmr_nbody_step_and_render: for every body i, acc = the
+ * sum over j of (p_j - p_i) m_j / (|p_j - p_i|^2 + eps2)^(3/2), taken in
+ * chunks of 1024 consecutive j (each chunk in order, then the chunk sums in
+ * order; FP32, exact sqrt and division), v += G acc dt, p' = p + v dt
+ * written to the other buffer, which is then
  * rendered (1-px splat fused into the same kernel) and made visible.  Needs
  * eps2 > 0 (it also removes the j = i term).  Advances the step counter. */
 MMR_API mmr_status mmr_alloc_nbody(mmr_ctx *ctx, float **dev_vel, float **dev_mass);

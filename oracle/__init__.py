@@ -54,7 +54,8 @@ _sig("orc_splat_h16", None, _u16p, C.c_int, C.c_uint64, _f32p, C.c_int, C.c_int,
      C.c_uint32, _u64p)
 _sig("orc_splat_disc_f32", None, _f32p, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
      C.c_uint32, _u64p)
-_sig("orc_nbody_step_f32", None, _f32p, _f32p, _f32p, _f32p, C.c_uint64, C.c_float, C.c_float, C.c_float)
+_sig("orc_nbody_step_f32", None, _f32p, _f32p, _f32p, _f32p, C.c_uint64, C.c_float, C.c_float, C.c_float,
+     C.c_uint64)
 _sig("orc_nbody_accel_f64", None, _f64p, _f64p, C.c_uint64, C.c_double, C.c_double, _f64p)
 _sig("orc_resolve", None, _u64p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_uint32, _u32p)
 
@@ -211,12 +212,15 @@ def render_disc(pos, M32, W, H, znear, zfar, radius, colors=None, color=0xFFFFFF
     return keys, resolve(keys, colors, color, background)
 
 
-def nbody_step_f32(pos, vel, mass, G, eps2, dt):
-    """One all-pairs gravity step (Sec. 4.2.3); returns the new positions,
-    updates vel in place."""
+NBODY_CHUNK = 1024
+
+
+def nbody_step_f32(pos, vel, mass, G, eps2, dt, chunk=NBODY_CHUNK):
+    """One all-pairs gravity step (Sec. 4.2.3), terms summed in chunks of
+    `chunk` bodies; returns the new positions, updates vel in place."""
     out = np.empty_like(pos)
     _lib.orc_nbody_step_f32(np.ascontiguousarray(pos, np.float32).reshape(-1), out.reshape(-1), vel.reshape(-1),
-                            np.ascontiguousarray(mass, np.float32), pos.shape[0], G, eps2, dt)
+                            np.ascontiguousarray(mass, np.float32), pos.shape[0], G, eps2, dt, chunk)
     return out
 
 

@@ -463,29 +463,39 @@ void orc_splat_disc_f32(const float *pos, uint64_t n, const float M[16], int W, 
 /* ------------------------------------------------------------------------ */
 /* Second workload: gravitational all-pairs N-body (the paper's N-body       */
 /* sample, Sec. 4.2.3), written from the physics.  Softened Newtonian        */
-/* gravity, for body i summed over j = 0 .. n-1 in order (the j = i term is  */
-/* zero):  d = p_j - p_i,  r2 = ((dx dx + dy dy) + dz dz) + eps2,            */
-/*         inv = 1 / sqrt(r2),  s = m_j ((inv inv) inv),  acc += d s;        */
-/* then a = G acc, v' = v + a dt, p' = p + v' dt (semi-implicit Euler).      */
+/* gravity; for body i the terms, j = 0 .. n-1,                              */
+/*   d = p_j - p_i,  r2 = ((dx dx + dy dy) + dz dz) + eps2,                  */
+/*   inv = 1 / sqrt(r2),  t_j = d (m_j ((inv inv) inv))   (zero for j = i),  */
+/* are summed in chunks of `chunk` consecutive j: each chunk in order of j   */
+/* from zero, then the chunk sums in chunk order from zero.  (The paper does */
+/* not fix an order; with one chunk this is the plain sequential sum.)       */
+/* Then a = G acc, v' = v + a dt, p' = p + v' dt (semi-implicit Euler).      */
 /* FP32, every operation rounded once, in that order; positions are read    */
 /* from pin and written to pout (two buffers, as the paper's ping-pong).     */
 /* ------------------------------------------------------------------------ */
 void orc_nbody_step_f32(const float *pin, float *pout, float *vel, const float *mass, uint64_t n, float G,
-                        float eps2, float dt)
+                        float eps2, float dt, uint64_t chunk)
 {
     for (uint64_t i = 0; i < n; ++i) {
         const float px = pin[3 * i], py = pin[3 * i + 1], pz = pin[3 * i + 2];
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        for (uint64_t j = 0; j < n; ++j) {
-            float dx = pin[3 * j] - px;
-            float dy = pin[3 * j + 1] - py;
-            float dz = pin[3 * j + 2] - pz;
-            float r2 = ((dx * dx + dy * dy) + dz * dz) + eps2;
-            float inv = 1.0f / sqrtf(r2);
-            float s = mass[j] * ((inv * inv) * inv);
-            ax = ax + dx * s;
-            ay = ay + dy * s;
-            az = az + dz * s;
+        for (uint64_t c0 = 0; c0 < n; c0 += chunk) {
+            const uint64_t c1 = c0 + chunk < n ? c0 + chunk : n;
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            for (uint64_t j = c0; j < c1; ++j) {
+                float dx = pin[3 * j] - px;
+                float dy = pin[3 * j + 1] - py;
+                float dz = pin[3 * j + 2] - pz;
+                float r2 = ((dx * dx + dy * dy) + dz * dz) + eps2;
+                float inv = 1.0f / sqrtf(r2);
+                float s = mass[j] * ((inv * inv) * inv);
+                sx = sx + dx * s;
+                sy = sy + dy * s;
+                sz = sz + dz * s;
+            }
+            ax = ax + sx;
+            ay = ay + sy;
+            az = az + sz;
         }
         float vx = vel[3 * i] + (G * ax) * dt;
         float vy = vel[3 * i + 1] + (G * ay) * dt;

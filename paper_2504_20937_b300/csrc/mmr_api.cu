@@ -40,6 +40,7 @@ struct mmr_ctx {
     uint32_t *colors = nullptr;
     float *nb_vel = nullptr;             // N-body workload: velocities (3n) and masses (n)
     float *nb_mass = nullptr;
+    float4 *nb_partial = nullptr;        // per-chunk partial sums (scratch)
     uint32_t *index = nullptr;           // indexed colour: colormap[index[id]]
     uint32_t *colormap = nullptr;
     uint32_t ncolors = 0;
@@ -362,6 +363,7 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
     dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
     dev_free(ctx, (void **)&ctx->nb_mass, ctx->n * 4);
+    dev_free(ctx, (void **)&ctx->nb_partial, (uint64_t)mmr::nbody_chunks((uint32_t)ctx->n) * ctx->n * 16);
     dev_free(ctx, (void **)&ctx->colormap, (uint64_t)ctx->ncolors * 4);
     dev_free(ctx, &ctx->rt_device, storage_bytes(ctx->n, ctx->dtype));
     if (ctx->rt_host) {
@@ -474,11 +476,15 @@ mmr_status mmr_alloc_nbody(mmr_ctx *ctx, float **dev_vel, float **dev_mass)
         return fail(ctx, MMR_ERR_STATE, "mmr_alloc_nbody: needs FP32 ping-pong buffers (mmr_alloc_pingpong)");
     if (ctx->nb_vel)
         return fail(ctx, MMR_ERR_STATE, "mmr_alloc_nbody: already allocated");
+    const uint64_t partial_bytes = (uint64_t)mmr::nbody_chunks((uint32_t)ctx->n) * ctx->n * 16;
     mmr_status st = dev_alloc(ctx, (void **)&ctx->nb_vel, ctx->n * 12, "N-body velocities");
     if (st == MMR_OK)
         st = dev_alloc(ctx, (void **)&ctx->nb_mass, ctx->n * 4, "N-body masses");
+    if (st == MMR_OK)
+        st = dev_alloc(ctx, (void **)&ctx->nb_partial, partial_bytes, "N-body partial sums");
     if (st != MMR_OK) {
         dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
+        dev_free(ctx, (void **)&ctx->nb_mass, ctx->n * 4);
         return st;
     }
     cudaError_t e = cudaMemset(ctx->nb_vel, 0, ctx->n * 12);
@@ -511,7 +517,7 @@ mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt
     if (ctx->timing)
         cudaEventRecord(ctx->ev[0], s);
     cudaError_t e = mmr::launch_nbody(static_cast<const float *>(ctx->buf[r]), static_cast<float *>(ctx->buf[r ^ 1]),
-                                      ctx->nb_vel, ctx->nb_mass, (uint32_t)ctx->n, B, P, s);
+                                      ctx->nb_vel, ctx->nb_mass, ctx->nb_partial, (uint32_t)ctx->n, B, P, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "N-body kernel launch");
     if (ctx->timing)
@@ -549,6 +555,7 @@ mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint32_t **d
         dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
     dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
     dev_free(ctx, (void **)&ctx->nb_mass, ctx->n * 4);
+    dev_free(ctx, (void **)&ctx->nb_partial, (uint64_t)mmr::nbody_chunks((uint32_t)ctx->n) * ctx->n * 16);
         return st;
     }
     ctx->ncolors = ncolors;

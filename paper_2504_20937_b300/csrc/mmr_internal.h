@@ -49,8 +49,10 @@ struct NbodyParams {
 };
 
 // One N-body step reading pin, writing pout and vel, splatting the new
-// positions into P.keys (FP32 positions, n bodies).
-cudaError_t launch_nbody(const float *pin, float *pout, float *vel, const float *mass, uint32_t n,
+// positions into P.keys (FP32 positions, n bodies).  `partial` is scratch of
+// nbody_chunks(n) * n float4 (the per-chunk sums).
+uint32_t nbody_chunks(uint32_t n);
+cudaError_t launch_nbody(const float *pin, float *pout, float *vel, const float *mass, float4 *partial, uint32_t n,
                          const NbodyParams &B, const PointParams &P, cudaStream_t s);
 
 // FP64 camera -> FP32 clip matrix (row-major 4x4); returns false on invalid input.

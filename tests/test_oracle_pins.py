@@ -472,6 +472,13 @@ def test_nbody_matches_fp64_brute_force_and_conserves_momentum():
     acc_np = float(G) * (d * (mass.astype(np.float64)[None, :] / r2 ** 1.5)[..., None]).sum(1)
     assert np.allclose(acc64, acc_np, rtol=1e-12, atol=1e-15)
     assert np.allclose(vel / float(dt), acc64, rtol=2e-4, atol=1e-6)
+    # the chunked order stays within FP32 rounding of the plain sequential sum
+    vel_seq = np.zeros_like(pos)
+    oracle.nbody_step_f32(pos, vel_seq, mass, G, eps2, dt, chunk=n)
+    vel_chunked = np.zeros_like(pos)
+    oracle.nbody_step_f32(pos, vel_chunked, mass, G, eps2, dt, chunk=7)
+    assert np.allclose(vel_chunked, vel_seq, rtol=1e-4, atol=1e-9)
+    assert not np.array_equal(vel_chunked, vel_seq)       # a different, but fixed, rounding order
     # pairwise forces cancel: total momentum stays at zero up to FP32 rounding
     p_tot = (mass[:, None].astype(np.float64) * vel.astype(np.float64)).sum(0)
     scale = (mass[:, None] * np.abs(vel)).sum(0)

@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_max_time_and_rate():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for rank in range(world):
         got, rate, _ = out[rank]
