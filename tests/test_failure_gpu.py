@@ -98,3 +98,14 @@ def test_budget_state_and_argument_errors():
         ctx.check_device()
     with pytest.raises(MmrError, match="INVALID"):
         Context(0, 10)
+
+
+def test_calls_after_close_are_rejected():
+    ctx = Context(16, 16)
+    ctx.alloc_points(10, "f32")
+    ctx.close()
+    with pytest.raises(MmrError, match="INVALID"):
+        ctx.step_and_render()
+    with pytest.raises(MmrError, match="INVALID"):
+        ctx.frame_ptrs()
+    ctx.close()                                            # closing twice is harmless

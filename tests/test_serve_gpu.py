@@ -172,3 +172,34 @@ def test_serve_request_loop_small_trace():
                         budget_bytes=(50_000 * 12 + 47) // 48 * 48 + 2 * (20_000 * 12 + 48 + 320 * 240 * 20))
     s2 = run_trace(trace, tight).summary()
     assert s2["frames"] == s["frames"] and s2["refused_for_budget"] > 0
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_serve_16bit_storage_matches_oracle(dtype):
+    """Shared and private clouds stored as binary16 / bfloat16."""
+    n_shared, n_priv, W, H, frames = 9_001, 2_003, 72, 40, 3
+    shared = inputs.encode(inputs.uniform_cloud(n_shared, 902), dtype)
+    priv = inputs.encode(inputs.uniform_cloud(n_priv, 903), dtype)
+    tv = lambda a: torch.from_numpy(a.view(np.int16))  # noqa: E731
+    with Server(n_shared, dtype, 55, 0, 1e-3) as srv:
+        srv.shared_points().copy_(tv(shared))
+        srv.set_shared_color(SHARED_COLOR)
+        v = srv.add_viewer(n_priv, W, H, seed=66, cloud=9, amplitude=1e-3, color=0xFF0000AA, background=3)
+        srv.viewer_points(v).copy_(tv(priv))
+        for k in range(frames):
+            srv.set_camera(v, _eye(1, k), CEN, UP, 60.0, 0.1, 100.0)
+            srv.tick()
+        torch.cuda.synchronize()
+        rgba, keys, _ = srv.frame(v)
+        gkeys = keys.cpu().numpy().reshape(-1).view(np.uint64)
+        grgba = rgba.cpu().numpy().reshape(-1).view(np.uint32)
+        gshared = srv.shared_points().cpu().numpy().view(np.uint16)
+    for t in range(frames):
+        oracle.displace(shared, dtype, 55, 0, t, np.float32(1e-3))
+        oracle.displace(priv, dtype, 66, 9, t, np.float32(1e-3))
+    assert np.array_equal(gshared, shared)
+    both = np.concatenate([shared, priv])
+    colors = np.concatenate([np.full(n_shared, SHARED_COLOR, np.uint32), np.full(n_priv, 0xFF0000AA, np.uint32)])
+    M = oracle.camera_f32(_eye(1, frames - 1), CEN, UP, 60.0, W / H, 0.1, 100.0)
+    keys, rgba = oracle.render(both, dtype, M, W, H, np.float32(0.1), np.float32(100.0), colors, 0, 3)
+    assert np.array_equal(gkeys, keys) and np.array_equal(grgba, rgba)
