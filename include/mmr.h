@@ -137,7 +137,7 @@ MMR_API mmr_status mmr_get_matrix(const mmr_ctx *ctx, float m[16]);
  * coordinate by amplitude * (2u - 1), u the top 24 bits of a
  * Philox4x32-10 draw with counter (point, step, cloud, 0) and key
  * (seed low, seed high) scaled by 2^-24, then clamps it to [0, 1].  The next
- * step index is first_step.  0 <= amplitude <= 1, finite. */
+ * step index is first_step.  amplitude is 0 or in [2^-100, 1]. */
 MMR_API mmr_status mmr_set_sim(mmr_ctx *ctx, uint64_t seed, uint32_t cloud, float amplitude,
                        uint32_t first_step);
 
@@ -260,7 +260,7 @@ typedef struct mmr_cloud_desc {
     int width, height;     /* this cloud's framebuffer, 1..32768 each */
     uint64_t seed;         /* Philox key (see mmr_set_sim) */
     uint32_t cloud;        /* Philox counter word 2 */
-    float amplitude;       /* displacement amplitude, [0, 1] */
+    float amplitude;       /* displacement amplitude, 0 or [2^-100, 1] */
     uint32_t color;        /* RGBA8 of every point */
     uint32_t background;   /* RGBA8 of empty pixels */
 } mmr_cloud_desc;

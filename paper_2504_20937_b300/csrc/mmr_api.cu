@@ -640,8 +640,8 @@ mmr_status mmr_set_sim(mmr_ctx *ctx, uint64_t seed, uint32_t cloud, float amplit
 {
     if (!ctx)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_sim: NULL ctx");
-    if (!(amplitude >= 0.0f && amplitude <= 1.0f))
-        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_sim: amplitude must be in [0, 1]");
+    if (!mmr::amplitude_ok(amplitude))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_sim: amplitude must be 0 or in [2^-100, 1]");
     ctx->seed = seed;
     ctx->cloud = cloud;
     ctx->amplitude = amplitude;

@@ -381,7 +381,7 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
     for (int c = 0; c < count; ++c) {
         const mmr_cloud_desc &d = clouds[c];
         if (d.n == 0 || d.n >= (1ull << 32) || d.width < 1 || d.height < 1 || d.width > 32768 ||
-            d.height > 32768 || !(d.amplitude >= 0.0f && d.amplitude <= 1.0f))
+            d.height > 32768 || !mmr::amplitude_ok(d.amplitude))
             return bfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_batch_create: cloud %d has an invalid descriptor", c);
     }
     mmr_batch *b = new (std::nothrow) mmr_batch();

@@ -38,6 +38,10 @@ cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cu
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
                            const Palette &pal, uint32_t npx, const LaunchShape &ls, cudaStream_t s);
 
+// Displacement amplitudes the kernels accept: 0, or [2^-100, 1] (so that
+// amplitude * 2^-23 is a normal float and the scaling is exact).
+inline bool amplitude_ok(float a) { return a == 0.0f || (a >= 0x1p-100f && a <= 1.0f); }
+
 // Message returned by mmr_last_error(NULL) on this thread.
 void set_process_error(const char *msg);
 

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(256) serve_private_kernel(ServeTables T)
         P.step = vw.step;
         P.cloud = vw.cloud;
         P.amplitude = vw.amplitude;
+        P.amplitude_2m23 = vw.amplitude * 0x1p-23f;
         P.id_base = T.id_base;
         P.ph_a = vw.ph_a;
         P.ph_b = vw.ph_b;
@@ -532,8 +533,8 @@ mmr_status mmr_serve_create(uint64_t shared_n, int dtype, uint64_t seed, uint32_
         return sfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_serve_create: shared_n outside 1..2^31-1");
     if (dtype != MMR_F32x3 && dtype != MMR_F16x3 && dtype != MMR_BF16x3)
         return sfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_serve_create: unknown dtype %d", dtype);
-    if (!(amplitude >= 0.0f && amplitude <= 1.0f))
-        return sfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_serve_create: amplitude must be in [0, 1]");
+    if (!mmr::amplitude_ok(amplitude))
+        return sfail(nullptr, MMR_ERR_INVALID_ARG, "mmr_serve_create: amplitude must be 0 or in [2^-100, 1]");
     mmr_serve *s = new (std::nothrow) mmr_serve();
     if (!s)
         return sfail(nullptr, MMR_ERR_OOM, "mmr_serve_create: host allocation failed");
@@ -597,7 +598,7 @@ mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int
         return sfail(s, MMR_ERR_INVALID_ARG, "mmr_serve_add_viewer: NULL argument");
     *viewer = -1;
     if (private_n == 0 || s->shared_n + private_n >= (1ull << 32) || width < 1 || height < 1 || width > 32768 ||
-        height > 32768 || !(amplitude >= 0.0f && amplitude <= 1.0f))
+        height > 32768 || !mmr::amplitude_ok(amplitude))
         return sfail(s, MMR_ERR_INVALID_ARG, "mmr_serve_add_viewer: invalid viewer description");
     const uint64_t npx = (uint64_t)width * height;
     Viewer v;
