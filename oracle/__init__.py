@@ -30,6 +30,7 @@ def _sig(name, res, *args):
 
 
 _sig("orc_philox4x32_10", None, _u32p, _u32p, _u32p)
+_sig("orc_philox4x32_10_many", None, _u32p, _u32p, _u32p, C.c_uint64)
 _sig("orc_displace_f32", None, _f32p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_float)
 _sig("orc_displace_ids_f32", None, _f32p, _u32p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
      C.c_float)
@@ -67,6 +68,15 @@ def philox4x32_10(ctr, key):
     """Philox4x32-10 of one counter (Salmon et al., SC'11)."""
     out = np.zeros(4, np.uint32)
     _lib.orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def philox4x32_10_many(ctr, key):
+    """Philox4x32-10 of uint32[n,4] counters with uint32[n,2] keys."""
+    ctr = np.ascontiguousarray(ctr, np.uint32)
+    key = np.ascontiguousarray(key, np.uint32)
+    out = np.empty_like(ctr)
+    _lib.orc_philox4x32_10_many(ctr.reshape(-1), key.reshape(-1), out.reshape(-1), ctr.shape[0])
     return out
 
 

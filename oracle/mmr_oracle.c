@@ -73,6 +73,13 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
+/* Philox4x32-10 of n counters with their keys (ctr: 4n words, key: 2n). */
+void orc_philox4x32_10_many(const uint32_t *ctr, const uint32_t *key, uint32_t *out, uint64_t n)
+{
+    for (uint64_t i = 0; i < n; ++i)
+        orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
 /* The three 32-bit draws that move point `i` at step `s` (Sec. 4.1). */
 static void draws_for_point(uint64_t seed, uint32_t cloud, uint32_t i, uint32_t s, uint32_t r[4])
 {
