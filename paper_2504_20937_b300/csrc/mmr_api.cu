@@ -452,6 +452,7 @@ mmr_status mmr_get_visible(const mmr_ctx *ctx, int *which)
 
 mmr_status mmr_step_and_render_pingpong(mmr_ctx *ctx, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_step_and_render_pingpong");
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = check_frame_ready(ctx, true);
@@ -501,6 +502,7 @@ mmr_status mmr_alloc_nbody(mmr_ctx *ctx, float **dev_vel, float **dev_mass)
 
 mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_nbody_step_and_render");
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = check_frame_ready(ctx, true);
@@ -688,6 +690,7 @@ mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel
 
 mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_step_and_render");
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = check_frame_ready(ctx, true);
@@ -699,6 +702,7 @@ mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream)
 
 mmr_status mmr_render(mmr_ctx *ctx, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_render");
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = check_frame_ready(ctx, true);
@@ -709,6 +713,7 @@ mmr_status mmr_render(mmr_ctx *ctx, void *stream)
 
 mmr_status mmr_displace(mmr_ctx *ctx, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_displace");
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = check_frame_ready(ctx, false);
@@ -725,6 +730,7 @@ mmr_status mmr_displace(mmr_ctx *ctx, void *stream)
 
 mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int pinned_host)
 {
+    mmr::NvtxRange nvtx("mmr_step_and_render_roundtrip");
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = check_frame_ready(ctx, true);

@@ -132,7 +132,7 @@ struct mmr_batch {
     uint64_t budget = 0;
     uint64_t held = 0;
     mmr::LaunchShape launch;
-    uint32_t chunk_groups = 256;
+    uint32_t chunk_groups = 128;
 
     std::vector<mmr_cloud_desc> desc;
     std::vector<uint64_t> pos_off;   // byte offset of each cloud's positions
@@ -401,8 +401,8 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
         delete b;
         return MMR_ERR_CUDA;
     }
-    b->launch.threads = 256;
-    b->launch.ctas_per_sm = 4;
+    b->launch.threads = 128;
+    b->launch.ctas_per_sm = 0;
     // layout: positions 256-byte aligned per cloud and padded to 48-byte groups
     for (int c = 0; c < count; ++c) {
         b->pos_off.push_back(b->pos_bytes);
@@ -540,6 +540,7 @@ mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_sm, int 
 
 mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_batch_step_and_render");
     if (!b)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = cameras_ready(b, false);
@@ -558,6 +559,7 @@ mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream)
 
 mmr_status mmr_batch_run_graph(mmr_batch *b, int frames, void *stream)
 {
+    mmr::NvtxRange nvtx("mmr_batch_run_graph");
     if (!b || frames < 0)
         return MMR_ERR_INVALID_ARG;
     mmr_status st = cameras_ready(b, true);
@@ -618,18 +620,20 @@ mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config,
     if (e == cudaSuccess)
         e = cudaEventCreate(&t1);
     st = e == cudaSuccess ? upload_cameras(b, s) : bcuda(b, e, "autotune set-up");
-    const int cand_threads[] = {128, 256, 512};
-    const int cand_ctas[] = {0, 1, 2, 4, 8};
-    const int cand_chunk[] = {64, 256, 1024};
+    // chunks are whole multiples of the block, so no thread of a CTA idles
+    const int cand_threads[] = {64, 128, 256};
+    const int cand_mult[] = {1, 2, 4};
+    const int cand_ctas[] = {0, 4, 8};
     float best = 1e30f;
     int bt = saved_launch.threads, bc = saved_launch.ctas_per_sm, bg = (int)saved_chunk;
-    for (int cg : cand_chunk) {
+    for (int th : cand_threads) {
         if (st != MMR_OK)
             break;
-        for (int th : cand_threads) {
+        for (int m : cand_mult) {
             if (st != MMR_OK)
                 break;
             for (int ct : cand_ctas) {
+                const int cg = th * m;
                 st = mmr_batch_set_launch(b, th, ct, cg);
                 if (st != MMR_OK)
                     break;

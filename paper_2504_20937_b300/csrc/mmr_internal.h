@@ -3,8 +3,18 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace mmr {
+
+// NVTX range around a host call, so profiler timelines show which library
+// call enqueued which kernels.  Header-only NVTX: no cost without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct PointParams;
 struct Palette;

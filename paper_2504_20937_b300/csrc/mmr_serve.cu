@@ -713,6 +713,7 @@ mmr_status mmr_serve_remove_viewer(mmr_serve *s, int viewer)
 
 static mmr_status serve_tick(mmr_serve *s, void *stream, int roundtrip)
 {
+    mmr::NvtxRange nvtx(roundtrip ? "mmr_serve_tick_roundtrip" : "mmr_serve_tick");
     if (!s)
         return MMR_ERR_INVALID_ARG;
     for (size_t k = 0; k < s->viewers.size(); ++k)

@@ -251,3 +251,34 @@ def test_disc_markers_bit_exact(dtype, radius):
     assert np.array_equal(gkeys, keys), f"{np.count_nonzero(gkeys != keys)} pixels differ"
     assert np.array_equal(grgba, rgba)
     assert (gkeys != oracle.EMPTY_KEY).sum() > 100          # the discs are really drawn
+
+
+def test_checkpoint_and_resume_is_bit_exact():
+    """State at step s is a pure function of (initial positions, seed, s):
+    a positions snapshot plus first_step resumes a run bit for bit."""
+    from paper_2504_20937_b300.api import Context
+    n, W, H, seed, a = 30_011, 80, 60, 21, 1e-3
+    stored = inputs.encode(inputs.uniform_cloud(n, 32), "f32")
+    eye = orbit(3.0)
+
+    def run(ctx, frames, first):
+        for f in range(first, first + frames):
+            ctx.set_camera(eye(f), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)
+            ctx.step_and_render()
+        torch.cuda.synchronize()
+
+    with Context(W, H) as ctx:
+        ctx.alloc_points(n, "f32").copy_(torch.from_numpy(stored))
+        ctx.set_sim(seed, 0, a, 0)
+        run(ctx, 6, 0)
+        snapshot, step = ctx.points.clone(), ctx.step
+        run(ctx, 5, 6)
+        want_pos = ctx.points.cpu().numpy()
+        want_rgba = ctx.frame_rgba().cpu().numpy()
+    assert step == 6
+    with Context(W, H) as ctx:
+        ctx.alloc_points(n, "f32").copy_(snapshot)
+        ctx.set_sim(seed, 0, a, step)
+        run(ctx, 5, 6)
+        assert np.array_equal(ctx.points.cpu().numpy(), want_pos)
+        assert np.array_equal(ctx.frame_rgba().cpu().numpy(), want_rgba)
