@@ -301,7 +301,7 @@ MMR_API mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream);
 MMR_API mmr_status mmr_batch_run_graph(mmr_batch *b, int frames, void *stream);
 
 /* Autotuner: times each candidate launch shape (threads in {64, 128, 256},
- * chunk groups = threads x {1, 2, 4}, CTAs per SM in {0, 4, 8}) over
+ * chunk groups = threads x {1, 2, 4, 8}, CTAs per SM in {0, 4, 8}) over
  * `frames_per_config` frames with CUDA events on `stream`, keeps the fastest
  * and returns it (any output pointer may be NULL).  Positions and the frame
  * counter are saved before and restored after, so the simulation state is

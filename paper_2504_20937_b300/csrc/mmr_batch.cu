@@ -57,48 +57,62 @@ struct BatchTables {
     uint32_t *frame;            // device frame counter
 };
 
-// At most 512 threads per block: the per-chunk cloud parameters held in
-// registers put this kernel above 64 registers per thread.
+// At most 512 threads per block (a bound the autotuner stays well below).
 constexpr int kBatchMaxThreads = 512;
 
+// One chunk's cloud parameters are built once per CTA in shared memory and
+// read from there by every thread: held in registers by each thread they
+// cost some 30 registers and halve the resident warps.
 template <int DT>
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_points_kernel(BatchTables T)
 {
+    constexpr uint32_t G = Group<DT>::kPoints;
+    __shared__ PointParams sP;
+    __shared__ uint32_t s_n;
+    __shared__ void *s_pos;
     const uint32_t frame = *T.frame;
     const uint32_t slot = frame % T.slots;
     const int buf = frame & 1;
     for (uint32_t c = blockIdx.x; c < T.n_point_chunks; c += gridDim.x) {
         const uint2 ch = T.point_chunks[c];
-        const CloudDev &cl = T.clouds[ch.x];
-        PointParams P;
-        P.cam = T.cams[(size_t)slot * T.count + ch.x];
-        P.keys = cl.keys[buf];
-        P.W = cl.W;
-        P.H = cl.H;
-        P.fW = cl.fW;
-        P.fH = cl.fH;
-        P.halfW = cl.halfW;
-        P.halfH = cl.halfH;
-        P.seed_lo = cl.seed_lo;
-        P.seed_hi = cl.seed_hi;
-        P.step = T.first_step + frame;
-        P.cloud = cl.cloud;
-        P.amplitude = cl.amplitude;
-        P.id_base = 0;
-        philox_prepare(P);
-        const uint32_t n = cl.n;
+        if (threadIdx.x == 0) {
+            const CloudDev &cl = T.clouds[ch.x];
+            PointParams P;
+            P.cam = T.cams[(size_t)slot * T.count + ch.x];
+            P.keys = cl.keys[buf];
+            P.W = cl.W;
+            P.H = cl.H;
+            P.fW = cl.fW;
+            P.fH = cl.fH;
+            P.halfW = cl.halfW;
+            P.halfH = cl.halfH;
+            P.seed_lo = cl.seed_lo;
+            P.seed_hi = cl.seed_hi;
+            P.step = T.first_step + frame;
+            P.cloud = cl.cloud;
+            P.amplitude = cl.amplitude;
+            P.id_base = 0;
+            philox_prepare(P);
+            sP = P;
+            s_n = cl.n;
+            s_pos = cl.pos;
+        }
+        __syncthreads();
+        const uint32_t n = s_n;
+        void *pos = s_pos;
+        const uint32_t full = n / G;
         const uint32_t end = min(ch.y + T.chunk_groups, groups_of<DT>(n));
-        const uint32_t full = n / Group<DT>::kPoints;
         for (uint32_t g = ch.y + threadIdx.x; g < end; g += blockDim.x) {
             if (g < full) {
                 uint4 q[3];
-                load_words(cl.pos, g, q);
-                process_words<DT, true, true>(q, g * Group<DT>::kPoints, Group<DT>::kPoints, P);
-                store_words(cl.pos, g, q);
+                load_words(pos, g, q);
+                process_words<DT, true, true>(q, g * G, G, sP);
+                store_words(pos, g, q);
             } else {
-                process_tail<DT, true, true>(cl.pos, cl.pos, n, g * Group<DT>::kPoints, P);
+                process_tail<DT, true, true>(pos, pos, n, g * G, sP);
             }
         }
+        __syncthreads();            // sP is rewritten for the next chunk
     }
 }
 
@@ -132,7 +146,7 @@ struct mmr_batch {
     uint64_t budget = 0;
     uint64_t held = 0;
     mmr::LaunchShape launch;
-    uint32_t chunk_groups = 128;
+    uint32_t chunk_groups = 256;
 
     std::vector<mmr_cloud_desc> desc;
     std::vector<uint64_t> pos_off;   // byte offset of each cloud's positions
@@ -401,7 +415,7 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
         delete b;
         return MMR_ERR_CUDA;
     }
-    b->launch.threads = 128;
+    b->launch.threads = 64;
     b->launch.ctas_per_sm = 0;
     // layout: positions 256-byte aligned per cloud and padded to 48-byte groups
     for (int c = 0; c < count; ++c) {
@@ -622,7 +636,7 @@ mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config,
     st = e == cudaSuccess ? upload_cameras(b, s) : bcuda(b, e, "autotune set-up");
     // chunks are whole multiples of the block, so no thread of a CTA idles
     const int cand_threads[] = {64, 128, 256};
-    const int cand_mult[] = {1, 2, 4};
+    const int cand_mult[] = {1, 2, 4, 8};
     const int cand_ctas[] = {0, 4, 8};
     float best = 1e30f;
     int bt = saved_launch.threads, bc = saved_launch.ctas_per_sm, bg = (int)saved_chunk;
