@@ -278,7 +278,7 @@ def run_ours(args, rank, world, local):
                    "storage": "f32", "amplitude": sc.amplitude, "orbit_deg_per_frame": sc.deg_per_frame,
                    "l2": f"flushed before every timed frame ({FLUSH_BYTES >> 20} MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": args.launch or "library default (grid-stride, 128 threads, one thread per 48-byte group)"},
+                   "launch": args.launch or "library default (grid-stride, 64 threads, one thread per 48-byte group)"},
         "frames_per_s": job_rate(args.steps, world, total_ms),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "hbm_gbs_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9,

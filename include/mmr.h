@@ -124,12 +124,16 @@ MMR_API mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint
  * with vertical field of view fovy_deg and aspect width/height.  Built in FP64
  * on the host and rounded once to FP32; a point is drawn only when
  * znear < clip w < zfar (clip w is its distance along the view axis).
- * Requires 0 < fovy_deg < 180, 0 < znear < zfar, eye != target. */
+ * Requires 0 < fovy_deg < 180, 2^-64 <= znear < zfar <= 2^64 (as FP32) and
+ * eye != target, else MMR_ERR_INVALID_ARG.  On that depth range the
+ * kernels' perspective divide (one shared reciprocal, Markstein's
+ * correction) gives every pixel that IEEE division gives. */
 MMR_API mmr_status mmr_set_camera(mmr_ctx *ctx, const double eye[3], const double target[3],
                           const double up[3], double fovy_deg, double znear, double zfar);
 
 /* Set the FP32 row-major 4x4 clip matrix directly (rows x, y and w are used)
- * and the depth range; mmr_get_matrix returns the matrix in use. */
+ * and the depth range; mmr_get_matrix returns the matrix in use.  Requires
+ * finite entries and 2^-64 <= znear < zfar <= 2^64, else MMR_ERR_INVALID_ARG. */
 MMR_API mmr_status mmr_set_matrix(mmr_ctx *ctx, const float m[16], float znear, float zfar);
 MMR_API mmr_status mmr_get_matrix(const mmr_ctx *ctx, float m[16]);
 
@@ -280,7 +284,8 @@ MMR_API const char *mmr_batch_last_error(const mmr_batch *b);
 MMR_API mmr_status mmr_batch_points(mmr_batch *b, int cloud, void **dev_ptr);
 
 /* Camera of `cloud` in slot `slot`, as mmr_set_camera with the cloud's own
- * aspect.  Uploaded to the device before the next step or graph replay. */
+ * aspect (same argument rules).  Uploaded to the device before the next
+ * step or graph replay. */
 MMR_API mmr_status mmr_batch_set_camera(mmr_batch *b, int cloud, int slot, const double eye[3],
                                         const double target[3], const double up[3], double fovy_deg,
                                         double znear, double zfar);
@@ -360,7 +365,8 @@ MMR_API mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int wi
                                         int *viewer);
 MMR_API mmr_status mmr_serve_viewer_points(mmr_serve *s, int viewer, void **dev_ptr);
 
-/* Camera of a viewer for the next tick (as mmr_set_camera, viewer aspect). */
+/* Camera of a viewer for the next tick (as mmr_set_camera, viewer aspect,
+ * same argument rules). */
 MMR_API mmr_status mmr_serve_set_camera(mmr_serve *s, int viewer, const double eye[3], const double target[3],
                                         const double up[3], double fovy_deg, double znear, double zfar);
 
@@ -409,7 +415,8 @@ MMR_API mmr_status mmr_serve_last_tick_ms(mmr_serve *s, float *ms);
  * what mmr_set_matrix + mmr_render produce for the same points.
  *  - Allocates nothing: no cudaMalloc, cudaFree or other allocating call.
  *  - width*height above MMR_STATIC_MAX_PIXELS, n outside 1..2^32-1, a NULL
- *    pointer or a misaligned dev_points: MMR_ERR_INVALID_ARG, nothing launched.
+ *    pointer, a misaligned dev_points or a depth range outside
+ *    2^-64 <= znear < zfar <= 2^64: MMR_ERR_INVALID_ARG, nothing launched.
  *  - The first call on a device (with that device current) looks up the
  *    array's device address once; make that first call before any CUDA
  *    stream capture that contains this call.

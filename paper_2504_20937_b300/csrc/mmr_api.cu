@@ -598,8 +598,8 @@ mmr_status mmr_set_matrix(mmr_ctx *ctx, const float m[16], float znear, float zf
 {
     if (!ctx || !m)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: NULL argument");
-    if (!(znear > 0.0f) || !(zfar > znear) || !std::isfinite(zfar))
-        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: need 0 < znear < zfar < inf");
+    if (!mmr::depth_range_ok(znear, zfar))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: need 2^-64 <= znear < zfar <= 2^64");
     for (int k = 0; k < 16; ++k)
         if (!std::isfinite(m[k]))
             return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_matrix: non-finite entry %d", k);
@@ -630,8 +630,9 @@ mmr_status mmr_set_camera(mmr_ctx *ctx, const double eye[3], const double target
 {
     if (!ctx || !eye || !target || !up)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: NULL argument");
-    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar))
-        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: need 0 < fovy < 180, 0 < znear < zfar");
+    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar) ||
+        !mmr::depth_range_ok((float)znear, (float)zfar))
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: need 0 < fovy < 180, 2^-64 <= znear < zfar <= 2^64");
     float m[16];
     if (!mmr::build_clip_matrix(eye, target, up, fovy_deg, (double)ctx->W / (double)ctx->H, znear, zfar, m))
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_camera: eye == target or up parallel to view");

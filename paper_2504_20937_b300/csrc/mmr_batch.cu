@@ -512,8 +512,10 @@ mmr_status mmr_batch_set_camera(mmr_batch *b, int cloud, int slot, const double 
 {
     if (!b || !eye || !target || !up || cloud < 0 || cloud >= b->count || slot < 0 || slot >= b->slots)
         return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_camera: bad argument");
-    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar))
-        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_camera: need 0 < fovy < 180, 0 < znear < zfar");
+    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar) ||
+        !mmr::depth_range_ok((float)znear, (float)zfar))
+        return bfail(b, MMR_ERR_INVALID_ARG,
+                     "mmr_batch_set_camera: need 0 < fovy < 180, 2^-64 <= znear < zfar <= 2^64");
     float m[16];
     const double aspect = (double)b->desc[cloud].width / (double)b->desc[cloud].height;
     if (!mmr::build_clip_matrix(eye, target, up, fovy_deg, aspect, znear, zfar, m))

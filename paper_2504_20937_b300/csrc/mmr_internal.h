@@ -69,6 +69,16 @@ uint32_t nbody_chunks(uint32_t n);
 cudaError_t launch_nbody(const float *pin, float *pout, float *vel, const float *mass, float4 *partial, uint32_t n,
                          const NbodyParams &B, const PointParams &P, cudaStream_t s);
 
+// The depth ranges a camera may use: 2^-64 <= znear < zfar <= 2^64 as FP32
+// values.  Kernels draw only points with znear < clip w < zfar, and on that
+// range of w their perspective divide (perspective_divide, one shared
+// reciprocal with Markstein's correction) gives every pixel that IEEE
+// division gives.
+inline bool depth_range_ok(float znear, float zfar)
+{
+    return znear >= 0x1p-64f && zfar > znear && zfar <= 0x1p64f;
+}
+
 // FP64 camera -> FP32 clip matrix (row-major 4x4); returns false on invalid input.
 bool build_clip_matrix(const double eye[3], const double target[3], const double up[3],
                        double fovy_deg, double aspect, double znear, double zfar, float out[16]);

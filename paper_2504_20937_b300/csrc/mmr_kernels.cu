@@ -13,29 +13,36 @@
 
 namespace mmr {
 
-// Grid-stride over 48-byte point groups.  With a persistent grid (fewer
-// threads than groups) each thread prefetches its next group into registers
-// before working on the current one, so a load is always in flight while the
-// thread computes; with one thread per group the loop runs once.  Positions
+// Grid-stride over 48-byte point groups.  On FP32 storage each thread
+// prefetches its next group into registers before working on the current
+// one, so a load is always in flight while the thread computes.  Positions
 // are read from src and the displaced ones written to dst: the same buffer
 // for an in-place step, the other ping-pong buffer otherwise.
 template <int DT, bool kDisplace, bool kSplat>
-__global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParams P)
+__device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t n, const PointParams &P)
 {
     constexpr int G = Group<DT>::kPoints;
+    constexpr bool kPrefetch = (DT == kF32);
     const uint32_t full = n / G;
     const uint32_t groups = groups_of<DT>(n);
     const uint32_t stride = gridDim.x * blockDim.x;
     uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     uint4 next[3];
-    if (g < full)
+    if (kPrefetch && g < full)
         load_words(src, g, next);
     while (g < groups) {
         const uint32_t gn = g + stride;
         if (g < full) {
-            uint4 q[3] = {next[0], next[1], next[2]};
-            if (gn < full)
-                load_words(src, gn, next);
+            uint4 q[3];
+            if constexpr (kPrefetch) {
+                q[0] = next[0];
+                q[1] = next[1];
+                q[2] = next[2];
+                if (gn < full)
+                    load_words(src, gn, next);
+            } else {
+                load_words(src, g, q);
+            }
             process_words<DT, kDisplace, kSplat>(q, g * G, G, P);
             if constexpr (kDisplace)
                 store_words(dst, g, q);
@@ -44,6 +51,24 @@ __global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParam
         }
         g = gn;
     }
+}
+
+// FP32 storage: the compiler's own register choice (48), measured fastest.
+template <bool kDisplace, bool kSplat>
+__global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParams P)
+{
+    points_body<kF32, kDisplace, kSplat>(src, dst, n, P);
+}
+
+// 16-bit storage.  A group holds 8 points, twice the work per load, so the
+// prefetch's 12 registers are better spent on resident warps: with it the
+// kernel needs 64 registers (32 warps per SM), without it and under this cap
+// 48 (40 warps), without spilling.  A register cap, unlike a launch bound,
+// leaves every block size up to 1024 valid.
+template <int DT, bool kDisplace, bool kSplat>
+__global__ void __maxnreg__(48) points_kernel_narrow(const void *src, void *dst, uint32_t n, PointParams P)
+{
+    points_body<DT, kDisplace, kSplat>(src, dst, n, P);
 }
 
 // Disc markers: as points_kernel (one thread per 48-byte group), each point
@@ -286,12 +311,21 @@ static cudaError_t launch_points_dt(const void *src, void *dst, uint32_t n, cons
 {
     const uint64_t groups = groups_of<DT>(n);
     const int grid = grid_for(groups, ls);
-    if (displace && splat)
-        points_kernel<DT, true, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
-    else if (displace)
-        points_kernel<DT, true, false><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
-    else
-        points_kernel<DT, false, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+    if constexpr (DT == kF32) {
+        if (displace && splat)
+            points_kernel<true, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+        else if (displace)
+            points_kernel<true, false><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+        else
+            points_kernel<false, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+    } else {
+        if (displace && splat)
+            points_kernel_narrow<DT, true, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+        else if (displace)
+            points_kernel_narrow<DT, true, false><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+        else
+            points_kernel_narrow<DT, false, true><<<grid, ls.threads, 0, s>>>(src, dst, n, P);
+    }
     return cudaGetLastError();
 }
 

@@ -76,8 +76,14 @@ __device__ __forceinline__ void view_params(const ViewDev &v, PointParams &P)
 }
 
 // Pass 1: the shared cloud, displaced once and splatted into every view.
+// The tick is bound by the latency of the depth tests into many views, so
+// resident warps matter: on FP32 storage a cap of 56 registers (from 58)
+// gives 9 blocks of 128 threads per SM instead of 8, without spilling.  The
+// 16-bit groups hold 24 coordinates across the view loop and need 69; their
+// cap of 72 only keeps them there (with no cap the compiler takes 80).
 template <int DT>
-__global__ void serve_shared_kernel(void *__restrict__ pos, uint32_t n, PointParams S, ServeTables T)
+__global__ void __maxnreg__(DT == kF32 ? 56 : 72)
+serve_shared_kernel(void *__restrict__ pos, uint32_t n, PointParams S, ServeTables T)
 {
     constexpr int G = Group<DT>::kPoints;
     const uint32_t full = n / G;
@@ -683,8 +689,10 @@ mmr_status mmr_serve_set_camera(mmr_serve *s, int viewer, const double eye[3], c
     Viewer *v = viewer_at(s, viewer);
     if (!v || !eye || !target || !up)
         return sfail(s, MMR_ERR_INVALID_ARG, "mmr_serve_set_camera: bad argument");
-    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar))
-        return sfail(s, MMR_ERR_INVALID_ARG, "mmr_serve_set_camera: need 0 < fovy < 180, 0 < znear < zfar");
+    if (!(fovy_deg > 0.0 && fovy_deg < 180.0) || !(znear > 0.0) || !(zfar > znear) || !std::isfinite(zfar) ||
+        !mmr::depth_range_ok((float)znear, (float)zfar))
+        return sfail(s, MMR_ERR_INVALID_ARG,
+                     "mmr_serve_set_camera: need 0 < fovy < 180, 2^-64 <= znear < zfar <= 2^64");
     float m[16];
     if (!mmr::build_clip_matrix(eye, target, up, fovy_deg, (double)v->W / (double)v->H, znear, zfar, m))
         return sfail(s, MMR_ERR_INVALID_ARG, "mmr_serve_set_camera: eye == target or up parallel to view");

@@ -87,8 +87,8 @@ extern "C" mmr_status mmr_render_static(const void *dev_points, uint64_t n, int 
     if (width < 1 || height < 1 || (uint64_t)width * (uint64_t)height > kStaticMaxPixels)
         return static_fail(MMR_ERR_INVALID_ARG,
                            "mmr_render_static: width*height must be 1..MMR_STATIC_MAX_PIXELS (4194304)");
-    if (!(znear > 0.0f) || !(zfar > znear))
-        return static_fail(MMR_ERR_INVALID_ARG, "mmr_render_static: need 0 < znear < zfar");
+    if (!mmr::depth_range_ok(znear, zfar))
+        return static_fail(MMR_ERR_INVALID_ARG, "mmr_render_static: need 2^-64 <= znear < zfar <= 2^64");
     if (reinterpret_cast<uintptr_t>(dev_points) % 16 != 0)
         return static_fail(MMR_ERR_INVALID_ARG, "mmr_render_static: dev_points must be 16-byte aligned");
     unsigned long long *keys = nullptr;

@@ -93,6 +93,36 @@ def test_launch_validation():
         ctx.check_device()
 
 
+def test_camera_depth_range_validation_and_extremes():
+    """Every camera keeps 2^-64 <= znear < zfar <= 2^64, the clip w range on
+    which the kernels' perspective divide gives IEEE division's pixels; the
+    ends of the range are allowed and render like the oracle."""
+    from paper_2504_20937_b300.api import Batch, Context, MmrError, Server
+    eye, centre, up = (0.5, 0.5, 2.5), (0.5, 0.5, 0.5), (0.0, 1.0, 0.0)
+    bad = [(2.0 ** -65, 1.0), (1e-30, 1.0), (0.1, 2.0 ** 65), (0.1, 1e30), (0.0, 1.0), (1.0, 1.0)]
+    with Context(16, 16) as ctx:
+        for zn, zf in bad:
+            with pytest.raises(MmrError, match="INVALID"):
+                ctx.set_camera(eye, centre, up, 60.0, zn, zf)
+            with pytest.raises(MmrError, match="INVALID"):
+                ctx.set_matrix(np.eye(4, dtype=np.float32), zn, zf)
+        ctx.set_camera(eye, centre, up, 60.0, 2.0 ** -64, 2.0 ** 64)
+        ctx.set_matrix(np.eye(4, dtype=np.float32), 2.0 ** -64, 2.0 ** 64)
+    with Batch([dict(n=100, width=8, height=8)]) as b:
+        with pytest.raises(MmrError, match="INVALID"):
+            b.set_camera(0, 0, eye, centre, up, 60.0, 1e-30, 1.0)
+    with Server(1000) as s:
+        v = s.add_viewer(10, 8, 8)
+        with pytest.raises(MmrError, match="INVALID"):
+            s.set_camera(v, eye, centre, up, 60.0, 0.1, 1e30)
+    n = 20_001
+    stored = inputs.encode(inputs.uniform_cloud(n, 41), "f32")
+    for zn, zf in ((2.0 ** -64, 2.0 ** 64), (2.0 ** -64, 3.0), (2.0, 2.0 ** 64)):
+        args = (stored, "f32", 120, 80, 6, 1e-3, 2, orbit(5.0))
+        kw = dict(znear=zn, zfar=zf)
+        _assert_same(gpu_run(*args, **kw), oracle_run(*args, **kw), f"depth range {zn}..{zf}")
+
+
 @pytest.mark.parametrize("mode", ["split", "roundtrip", "roundtrip_pageable"])
 def test_split_and_roundtrip_paths_match(mode):
     n = 50_003
