@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=["c2", "pr1", "c3"])
     ap.add_argument("--no-extra", action="store_true", help="skip the 64M-point and round-trip legs")
     ap.add_argument("--cpu-frames", type=int, default=60, help="oracle frames for the CPU baseline (0: skip)")
+    ap.add_argument("--cpu-omp-seconds", type=float, default=8.0,
+                    help="seconds of OpenMP CPU-baseline frames on all host cores (0: skip)")
     ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
     ap.add_argument("--launch", default="", help="threads,ctas_per_sm,kernel for the point kernel (default: library's)")
     return ap.parse_args()
@@ -247,8 +249,10 @@ def run_ours(args, rank, world, local):
                 resolve_ms.append(rk)
         return step_ms, point_ms, resolve_ms
 
+    free_before = torch.cuda.mem_get_info(local)[0]
     ctx = make_ctx()
     zero_copy_bytes = ctx.device_bytes
+    zero_copy_measured = free_before - torch.cuda.mem_get_info(local)[0]   # cudaMemGetInfo delta
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -289,7 +293,7 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes_per_launch": bytes_point},
         "gpu_launches": 2 * args.steps,
         "wall_s_timed_region": wall,
-        "device_bytes": {"zero_copy": zero_copy_bytes},
+        "device_bytes": {"zero_copy": zero_copy_bytes, "zero_copy_cudaMemGetInfo": zero_copy_measured},
     }
     clocks = clk.summary()
     if clocks:
@@ -300,6 +304,7 @@ def run_ours(args, rank, world, local):
         rt_frames = min(args.steps, 200)
         rt_ms, _, _ = timed_frames(ctx, sc, rt_frames, 3, True, roundtrip=True)
         out["device_bytes"]["roundtrip"] = ctx.device_bytes
+        out["device_bytes"]["roundtrip_cudaMemGetInfo"] = free_before - torch.cuda.mem_get_info(local)[0]
         out["roundtrip_pinned"] = {"points_per_s": rt_frames * n / (sum(rt_ms) / 1e3),
                                    "frames_per_s": rt_frames / (sum(rt_ms) / 1e3),
                                    "p50_ms": float(np.percentile(rt_ms, 50)),
@@ -522,6 +527,30 @@ def cpu_oracle_rate(sc, stored, frames, points):
     return frames * points / dt, dt
 
 
+def cpu_omp_rate(sc, stored, seconds):
+    """The oracle's frame over all host cores (OpenMP, oracle/mmr_cpu_omp.c):
+    whole frames of the full workload, one untimed, then as many as fit in
+    `seconds` (at least 3).  The frames equal the oracle's bit for bit."""
+    import oracle
+    pos = stored.copy()
+    keys = np.empty(sc.W * sc.H, np.uint64)
+    rgba = np.empty(sc.W * sc.H, np.uint32)
+
+    def frame(f):
+        M = oracle.camera_f32(sc.eye(f), CENTRE, UP, sc.fovy_deg, sc.aspect, sc.znear, sc.zfar)
+        return oracle.cpu_omp_frame_f32(pos, sc.philox_seed, 0, f, sc.amplitude, M, sc.W, sc.H, sc.znear,
+                                        sc.zfar, keys=keys, rgba=rgba)[2]
+
+    threads = frame(0)
+    t0 = time.perf_counter()
+    frames = 0
+    while frames < 3 or time.perf_counter() - t0 < seconds:
+        frame(1 + frames)
+        frames += 1
+    dt = time.perf_counter() - t0
+    return frames * sc.n / dt, dt, frames, threads
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -564,6 +593,14 @@ def main():
             out["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
                                    "sample": f"{frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the "
                                              f"workload on one host core, {dt:.1f} s"}
+        if args.cpu_omp_seconds > 0:
+            sc = scene_for(args.workload, args.points)
+            stored = inputs.encode(sc.positions(), "f32")
+            rate, dt, frames, threads = cpu_omp_rate(sc, stored, args.cpu_omp_seconds)
+            out["cpu_baseline_openmp"] = {
+                "value": rate, "unit": "points/s", "cores": threads, "kind": "oracle routines over OpenMP threads",
+                "sample": f"{frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the workload, {dt:.1f} s; "
+                          f"host reports {os.cpu_count()} logical CPUs"}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

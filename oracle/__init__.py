@@ -270,3 +270,44 @@ def run_frames(pos, dtype, seed, cloud, a, first_step, frames, cam_for_frame, W,
         displace(pos, dtype, seed, cloud, first_step + f, a)
         keys, rgba = render(pos, dtype, cam_for_frame(f), W, H, znear, zfar, colors, color, background)
     return keys, rgba
+
+
+# -- OpenMP CPU baseline (mmr_cpu_omp.c): the oracle's routines over all host
+# cores, for bench.py's multi-core CPU figure.  Loaded on first use.
+_omp = None
+
+
+def _omp_lib():
+    global _omp
+    if _omp is None:
+        lib = C.CDLL(_build.build_omp())
+        lib.cpu_omp_frame_f32.restype = C.c_int
+        lib.cpu_omp_frame_f32.argtypes = [_f32p, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_float,
+                                          _f32p, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint32, C.c_uint32,
+                                          _u64p, _u32p, C.c_int]
+        lib.cpu_omp_threads.restype = C.c_int
+        lib.cpu_omp_threads.argtypes = [C.c_int]
+        _omp = lib
+    return _omp
+
+
+def cpu_omp_threads(threads=0):
+    """Threads cpu_omp_frame_f32 uses for `threads` (0: OpenMP's default)."""
+    return _omp_lib().cpu_omp_threads(threads)
+
+
+def cpu_omp_frame_f32(pos, seed, cloud, step, a, M32, W, H, znear, zfar, color=0xFFFFFFFF, background=0,
+                      threads=0, keys=None, rgba=None):
+    """One FP32 frame (displace at `step`, clear, splat, resolve with one
+    colour) on `threads` host threads; pos is updated in place.  Returns
+    (keys, rgba, threads used); equal to the oracle's frame bit for bit."""
+    assert pos.dtype == np.float32 and pos.flags.c_contiguous
+    if keys is None:
+        keys = np.empty(W * H, np.uint64)
+    if rgba is None:
+        rgba = np.empty(W * H, np.uint32)
+    used = _omp_lib().cpu_omp_frame_f32(pos.reshape(-1), pos.shape[0], seed, cloud, step, np.float32(a),
+                                        np.ascontiguousarray(M32, np.float32).reshape(-1), W, H,
+                                        np.float32(znear), np.float32(zfar), color, background, keys, rgba,
+                                        threads)
+    return keys, rgba, used
