@@ -312,3 +312,38 @@ def test_checkpoint_and_resume_is_bit_exact():
         run(ctx, 5, 6)
         assert np.array_equal(ctx.points.cpu().numpy(), want_pos)
         assert np.array_equal(ctx.frame_rgba().cpu().numpy(), want_rgba)
+
+
+@pytest.mark.parametrize("radius", [0.5, 1.0, 1.5, 2.0, 3.0, 64.0])
+@pytest.mark.parametrize("W,H", [(64, 64), (61, 37)])
+def test_disc_markers_at_exact_pixel_distances(radius, W, H):
+    """Disc centres exactly on pixel centres and pixel edges and one ulp or
+    2^-20 either side of them, so many candidate pixels sit exactly at, or a
+    rounding away from, distance r; discs partly off the frame.  With the
+    clip matrix x, y -> (x, y, w = 1) the screen position is (x + 1) W/2,
+    (1 - y) H/2.  Rendered (no displacement) against the oracle's wide
+    candidate box, bit for bit: the kernel's tighter box must hold every
+    pixel that passes."""
+    from paper_2504_20937_b300.api import Context
+    base = np.arange(-110, 111, dtype=np.float64) / 64.0           # screen offsets in half pixels
+    vals = set()
+    for v in base.astype(np.float32):
+        for d in (np.float32(0), np.float32(2.0 ** -20)):
+            vals.update({np.float32(v + d), np.float32(v - d)})
+        vals.update({np.nextafter(v, np.float32(2)), np.nextafter(v, np.float32(-2))})
+    vals = np.array(sorted(vals), dtype=np.float32)
+    rng = np.random.default_rng(int(radius * 8) + W)
+    xs = rng.choice(vals, 4000)
+    ys = rng.choice(vals, 4000)
+    pos = np.stack([xs, ys, np.zeros_like(xs)], axis=1).astype(np.float32)
+    M = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1]], dtype=np.float32)
+    with Context(W, H) as ctx:
+        ctx.alloc_points(len(pos), "f32").copy_(torch.from_numpy(pos))
+        ctx.set_matrix(M, 0.5, 2.0)
+        ctx.set_marker(radius)
+        ctx.render()
+        torch.cuda.synchronize()
+        gkeys = ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64)
+    keys, _ = oracle.render_disc(pos, M.reshape(-1), W, H, np.float32(0.5), np.float32(2.0), np.float32(radius))
+    assert np.array_equal(gkeys, keys), f"{np.count_nonzero(gkeys != keys)} pixels differ"
+    assert (keys != oracle.EMPTY_KEY).sum() > W * H // 4
