@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--cpu-omp-seconds", type=float, default=8.0,
                     help="seconds of OpenMP CPU-baseline frames on all host cores (0: skip)")
     ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
+    ap.add_argument("--leg", default="all", choices=["all", "batched", "served"],
+                    help="run one leg alone (profiling cases): batched = the 256-cloud batch for --steps frames, "
+                         "served = the zero-copy serving trace of --serve-requests requests")
+    ap.add_argument("--serve-requests", type=int, default=10_000, help="frame requests of the serving trace")
     ap.add_argument("--launch", default="", help="threads,ctas_per_sm,kernel for the point kernel (default: library's)")
     return ap.parse_args()
 
@@ -334,7 +338,7 @@ def run_ours(args, rank, world, local):
         out["features_c2"] = run_features(sc, stored, hbm_gbs)
         out["nbody"] = run_nbody()
         out["batched_256_clouds"] = run_batched(hbm_gbs)
-        out["served"] = run_served()
+        out["served"] = run_served(args.serve_requests)
     else:
         ctx.close()
     return out
@@ -492,7 +496,7 @@ def run_batched(hbm_gbs, frames=100):
             "launch": "one persistent point launch + one persistent resolve launch + counter, replayed as a CUDA graph"}
 
 
-def run_served(requests=10_000):
+def run_served(requests=10_000, roundtrip=True):
     """Continuous batching: shared 2^24-point cloud, Poisson viewer arrivals,
     private clouds 1e4..1e6 points, 640x480 / 1920x1080 / 3840x2160, up to 64
     concurrent viewers under a 40 GB budget; zero-copy vs the host round trip
@@ -503,7 +507,7 @@ def run_served(requests=10_000):
     shared = inputs.encode(inputs.uniform_cloud(cfg.shared_n, cfg.shared_seed), cfg.dtype)
     clouds = {r.viewer: serve.private_cloud(r, cfg.dtype) for r in trace}
     zero = serve.run_trace(trace, cfg, clouds=clouds, shared=shared).summary()
-    rt = serve.run_trace(trace, cfg, roundtrip=True, clouds=clouds, shared=shared).summary()
+    rt = serve.run_trace(trace, cfg, roundtrip=True, clouds=clouds, shared=shared).summary() if roundtrip else None
     return {"requests": requests, "viewers": len(trace), "shared_points": cfg.shared_n,
             "max_concurrent": cfg.max_viewers, "budget_gb": cfg.budget_bytes / 2**30,
             "zero_copy": zero, "roundtrip": rt,
@@ -577,6 +581,15 @@ def main():
         out = run_reference(args, rank, world)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.leg != "all":
+        # one leg alone, on one GPU: a small, self-contained command for profilers
+        hbm_gbs, _ = measured_peaks()
+        if args.leg == "batched":
+            res = run_batched(hbm_gbs, frames=args.steps)
+        else:
+            res = run_served(args.serve_requests, roundtrip=False)
+        print(json.dumps({"leg": args.leg, args.leg: res}), flush=True)
         return
     if world > 1:
         import torch
