@@ -203,3 +203,58 @@ def test_serve_16bit_storage_matches_oracle(dtype):
     M = oracle.camera_f32(_eye(1, frames - 1), CEN, UP, 60.0, W / H, 0.1, 100.0)
     keys, rgba = oracle.render(both, dtype, M, W, H, np.float32(0.1), np.float32(100.0), colors, 0, 3)
     assert np.array_equal(gkeys, keys) and np.array_equal(grgba, rgba)
+
+
+def test_serve_full_size_sampled():
+    """The serving configuration at full size: the 2^24-point shared cloud
+    and viewers at 3840x2160, 1920x1080 and 640x480 with private clouds of
+    1e6, 1e5 and 1e4 points, the third joining one tick later; three ticks.
+    Every viewer's last frame and the shared positions against the oracle,
+    bit for bit."""
+    cfg = ServeConfig()
+    amp = np.float32(cfg.amplitude)
+    shared0 = inputs.encode(inputs.uniform_cloud(cfg.shared_n, cfg.shared_seed), "f32")
+    viewers = [(1_000_000, 3840, 2160, 0), (100_000, 1920, 1080, 0), (10_000, 640, 480, 1)]
+    ticks = 3
+    got = {}
+    with Server(cfg.shared_n, "f32", cfg.shared_seed, 0, cfg.amplitude) as srv:
+        srv.shared_points().copy_(torch.from_numpy(shared0))
+        srv.set_shared_color(SHARED_COLOR)
+        ids, done = {}, {}
+        for tick in range(ticks):
+            for v, (n, W, H, join) in enumerate(viewers):
+                if join == tick:
+                    ids[v] = srv.add_viewer(**_viewer_args(v, n, W, H))
+                    srv.viewer_points(ids[v]).copy_(torch.from_numpy(_private(v, n)))
+                    done[v] = 0
+            for v, vid in ids.items():
+                srv.set_camera(vid, _eye(v, done[v]), CEN, UP, 60.0, 0.1, 100.0)
+            srv.tick()
+            for v in ids:
+                done[v] += 1
+        torch.cuda.synchronize()
+        for v, vid in ids.items():
+            rgba, keys, f = srv.frame(vid)
+            assert f == done[v]
+            got[v] = (done[v], keys.cpu().numpy().reshape(-1).view(np.uint64),
+                      rgba.cpu().numpy().reshape(-1).view(np.uint32))
+        shared_gpu = srv.shared_points().cpu().numpy()
+    shared = shared0.copy()
+    for t in range(ticks):
+        oracle.displace_f32(shared, cfg.shared_seed, 0, t, amp)
+    assert np.array_equal(shared_gpu, shared), "shared positions"
+    for v, (n, W, H, join) in enumerate(viewers):
+        frames, gkeys, grgba = got[v]
+        priv = _private(v, n)
+        for s in range(frames):
+            oracle.displace_f32(priv, 3000 + v, 1 + v, s, AMP)      # the private amplitude of _viewer_args
+        both = np.concatenate([shared, priv])
+        colors = np.concatenate([np.full(cfg.shared_n, SHARED_COLOR, np.uint32),
+                                 np.full(n, 0xFF000000 | v, np.uint32)])
+        M = oracle.camera_f32(_eye(v, frames - 1), CEN, UP, 60.0, W / H, 0.1, 100.0)
+        keys, rgba = oracle.render(both, "f32", M, W, H, np.float32(0.1), np.float32(100.0), colors, 0, 0x10 + v)
+        bad = np.nonzero(gkeys != keys)[0]
+        assert bad.size == 0, (f"keys of viewer {v} ({W}x{H}): {bad.size} pixels differ, first {bad[:4]}, "
+                               f"gpu {[hex(int(x)) for x in gkeys[bad[:4]]]}, oracle {[hex(int(x)) for x in keys[bad[:4]]]}")
+        assert np.array_equal(grgba, rgba), f"rgba of viewer {v} ({W}x{H})"
+        assert (keys != oracle.EMPTY_KEY).sum() > W * H // 20
