@@ -660,6 +660,17 @@ def main():
             out["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
                                    "sample": f"{frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the "
                                              f"workload on one host core, {dt:.1f} s"}
+        if args.cpu_frames > 0 and not args.no_extra:
+            # the oracle on one core for the other two single-cloud configurations: the whole 100-step
+            # reference run, and three frames of the 64M-point 4K frame (per-frame time)
+            cfgs = {}
+            pr1 = inputs.PR1
+            rate, dt = cpu_oracle_rate(pr1, inputs.encode(pr1.positions(), "f32"), pr1.frames, pr1.n)
+            cfgs[pr1.name] = {"points_per_s": rate, "seconds": dt, "frames": pr1.frames, "cores": 1}
+            c3 = inputs.C3
+            rate, dt = cpu_oracle_rate(c3, inputs.encode(c3.positions(), "f32"), 3, c3.n)
+            cfgs[c3.name] = {"points_per_s": rate, "ms_per_frame": dt / 3 * 1e3, "frames": 3, "cores": 1}
+            out["cpu_baseline_configs"] = cfgs
         if args.cpu_omp_seconds > 0:
             sc = scene_for(args.workload, args.points)
             stored = inputs.encode(sc.positions(), "f32")
