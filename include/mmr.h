@@ -10,8 +10,8 @@
  * section (Sec. 3.4, Listing 2) become stream ordering: every call that takes
  * a stream only enqueues work on it, and a frame is valid once that stream
  * has been synchronised.  The paper draws through Vulkan; here projection and
- * a depth-tested 1-px splat are CUDA kernels writing a framebuffer that stays
- * in device memory.
+ * a depth-tested splat (1 px, or a disc of a chosen radius) are CUDA kernels
+ * writing a framebuffer that stays in device memory.
  *
  * Conventions for every entry point:
  *  - Pointers named dev_* or returned as device pointers are GPU addresses of
@@ -159,8 +159,10 @@ MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t backgrou
  *  kernel = MMR_KERNEL_GRID: grid-stride over 48-byte point groups with
  *    `threads` per block (a multiple of 32, 32..1024); ctas_per_sm = 0 gives
  *    one thread per group, ctas_per_sm > 0 a persistent grid of
- *    sm_count * ctas_per_sm CTAs in which every thread prefetches its next
- *    group while working on the current one.
+ *    sm_count * ctas_per_sm CTAs.  On FP32 storage every thread of such a
+ *    grid prefetches its next group while working on the current one; the
+ *    16-bit kernels load each group when they reach it, to stay at 48
+ *    registers.
  *  kernel = MMR_KERNEL_TMA: persistent, TMA-staged (threads 128, 256 or
  *    512; ctas_per_sm >= 1): each CTA keeps 4 tiles of threads*48 bytes in
  *    flight through shared memory with bulk copies.
