@@ -184,6 +184,17 @@ def test_single_pixel_framebuffer_and_tall_frame():
         _assert_same(gpu_run(*args), oracle_run(*args), f"{W}x{H}")
 
 
+@pytest.mark.parametrize("W,H", [(32768, 32), (16384, 4096)])
+def test_large_frames_bit_exact(W, H):
+    """The widest frame allowed and a 67M-pixel frame (pixel indices past
+    2^26, a resolve grid of 16.8M quads), bit for bit."""
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(1 << 21, 29, components=8, sigma=0.1), "f32")
+    args = (stored, "f32", W, H, 4, 1e-3, 2, orbit(9.0))
+    g, o = gpu_run(*args), oracle_run(*args)
+    _assert_same(g, o, f"{W}x{H}")
+    assert (o[1] != oracle.EMPTY_KEY).sum() > 100       # at 1024:1 the cloud is a few hundred pixels wide
+
+
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
 def test_pingpong_matches_in_place_and_keeps_previous_state(dtype):
     """Out-of-place stepping into the other buffer (the paper's alternating
