@@ -360,8 +360,12 @@ MMR_API mmr_status mmr_serve_set_shared_color(mmr_serve *s, uint32_t color);
 /* Admit a viewer: private cloud of private_n points (zero-filled; write it
  * through mmr_serve_viewer_points before its first tick), a width x height
  * framebuffer, its own Philox key/cloud word/amplitude and colours.  Returns
- * the viewer id in *viewer.  MMR_ERR_BUDGET when it does not fit (nothing is
- * allocated then).  shared_n + private_n must stay below 2^32. */
+ * the viewer id in *viewer.  MMR_ERR_BUDGET when its buffers do not fit
+ * beside those of the active viewers (nothing is allocated then).
+ * shared_n + private_n must stay below 2^32.  Buffers kept from viewers
+ * that left are reused when their size fits (a buffer at most twice the
+ * size needed); they are cleared on the engine's own stream, so a join does
+ * not wait for a tick in flight, and the call returns once they are clear. */
 MMR_API mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int height, uint64_t seed,
                                         uint32_t cloud, float amplitude, uint32_t color, uint32_t background,
                                         int *viewer);
@@ -372,7 +376,10 @@ MMR_API mmr_status mmr_serve_viewer_points(mmr_serve *s, int viewer, void **dev_
 MMR_API mmr_status mmr_serve_set_camera(mmr_serve *s, int viewer, const double eye[3], const double target[3],
                                         const double up[3], double fovy_deg, double znear, double zfar);
 
-/* Release a viewer's memory after the last enqueued tick has finished. */
+/* Remove a viewer once the last enqueued tick has finished.  Its buffers are
+ * kept by the engine for later joins (still counted in the device bytes and
+ * against the budget); they are freed when a join needs the room under the
+ * budget, when an allocation fails, or at mmr_serve_destroy. */
 MMR_API mmr_status mmr_serve_remove_viewer(mmr_serve *s, int viewer);
 
 /* One tick on `stream` (every active viewer needs a camera).  The
@@ -385,7 +392,8 @@ MMR_API mmr_status mmr_serve_tick_roundtrip(mmr_serve *s, void *stream);
 MMR_API mmr_status mmr_serve_frame_ptr(mmr_serve *s, int viewer, const uint32_t **rgba, const uint64_t **depth_id,
                                        uint32_t *frame_index);
 
-/* Ticks so far, active viewers, device bytes held (any pointer may be NULL). */
+/* Ticks so far, active viewers, device bytes held, kept buffers of departed
+ * viewers included (any pointer may be NULL). */
 MMR_API mmr_status mmr_serve_status(const mmr_serve *s, uint32_t *tick, int *active_viewers,
                                     uint64_t *device_bytes);
 

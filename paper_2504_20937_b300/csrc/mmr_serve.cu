@@ -20,6 +20,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <iterator>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -221,7 +223,8 @@ struct Viewer {
     uint64_t pos_bytes = 0;
     unsigned long long *keys[2] = {nullptr, nullptr};
     uint32_t *rgba = nullptr;
-    uint64_t bytes = 0;             // everything this viewer holds
+    uint64_t cap_pos = 0, cap_keys[2] = {0, 0}, cap_rgba = 0;  // sizes of the buffers held (>= what is used)
+    uint64_t bytes = 0;             // everything this viewer needs
     uint32_t frames = 0;            // frames rendered = next private step
     uint32_t joined_tick = 0;
     mmr::Cam cam{};
@@ -262,6 +265,14 @@ struct mmr_serve {
     // host round-trip baseline buffers
     void *rt_host = nullptr;
     uint64_t rt_cap = 0;
+
+    // Buffers of viewers that left, kept for the next joins (size in bytes -> pointer) instead of being freed:
+    // cudaMalloc and cudaFree cost host time on every join and leave, and cudaFree waits for the whole device.
+    // They stay counted in `held`; `cached` is their total.  No tick in flight uses them (a leave waits for
+    // the last tick).
+    std::multimap<uint64_t, void *> cache;
+    uint64_t cached = 0;
+    cudaStream_t aux = nullptr;     // non-blocking: clears a joining viewer's buffers without waiting for a tick
 
     char err[512] = "";
 };
@@ -311,6 +322,54 @@ void sfree(mmr_serve *s, void **p, uint64_t bytes, bool budgeted = true)
             s->held -= bytes;
         *p = nullptr;
     }
+}
+
+// Free cached buffers, largest first, until `need` more bytes fit the budget (all of them for UINT64_MAX).
+void trim_cache(mmr_serve *s, uint64_t need)
+{
+    while (!s->cache.empty() && (need == UINT64_MAX || (s->budget && s->held + need > s->budget))) {
+        auto it = std::prev(s->cache.end());
+        cudaFree(it->second);
+        s->held -= it->first;
+        s->cached -= it->first;
+        s->cache.erase(it);
+    }
+}
+
+// A viewer buffer of at least `bytes`: the smallest cached one of at most
+// twice that size, else a new allocation (after trimming the cache to fit
+// the budget, and once more after an out-of-memory failure).  *cap gets the
+// buffer's size.
+mmr_status vtake(mmr_serve *s, void **p, uint64_t bytes, uint64_t *cap, const char *what)
+{
+    auto it = s->cache.lower_bound(bytes);
+    if (it != s->cache.end() && it->first <= 2 * bytes) {
+        *p = it->second;
+        *cap = it->first;
+        s->cached -= it->first;
+        s->cache.erase(it);
+        return MMR_OK;
+    }
+    trim_cache(s, bytes);
+    mmr_status st = salloc(s, p, bytes, what);
+    if (st == MMR_ERR_OOM && !s->cache.empty()) {
+        trim_cache(s, UINT64_MAX);
+        st = salloc(s, p, bytes, what);
+    }
+    if (st == MMR_OK)
+        *cap = bytes;
+    return st;
+}
+
+// Return a viewer buffer to the cache.
+void vgive(mmr_serve *s, void **p, uint64_t *cap)
+{
+    if (*p) {
+        s->cache.emplace(*cap, *p);
+        s->cached += *cap;
+    }
+    *p = nullptr;
+    *cap = 0;
 }
 
 uint64_t padded_point_bytes(uint64_t n, int dtype)
@@ -486,11 +545,10 @@ cudaError_t launch_tick(mmr_serve *S, const mmr::ServeTables &T, cudaStream_t s,
 
 void release_viewer(mmr_serve *S, Viewer &v)
 {
-    const uint64_t npx = (uint64_t)v.W * v.H;
-    sfree(S, &v.pos, v.pos_bytes);
-    sfree(S, (void **)&v.keys[0], npx * 8);
-    sfree(S, (void **)&v.keys[1], npx * 8);
-    sfree(S, (void **)&v.rgba, npx * 4);
+    vgive(S, &v.pos, &v.cap_pos);
+    vgive(S, (void **)&v.keys[0], &v.cap_keys[0]);
+    vgive(S, (void **)&v.keys[1], &v.cap_keys[1]);
+    vgive(S, (void **)&v.rgba, &v.cap_rgba);
     v = Viewer{};
 }
 
@@ -508,6 +566,9 @@ mmr_status mmr_serve_destroy(mmr_serve *s)
     for (Viewer &v : s->viewers)
         if (v.active)
             release_viewer(s, v);
+    trim_cache(s, UINT64_MAX);
+    if (s->aux)
+        cudaStreamDestroy(s->aux);
     sfree(s, &s->shared_pos, s->shared_bytes);
     sfree(s, (void **)&s->d_views, s->cap_views, false);
     sfree(s, (void **)&s->d_pchunks, s->cap_pchunks, false);
@@ -568,6 +629,8 @@ mmr_status mmr_serve_create(uint64_t shared_n, int dtype, uint64_t seed, uint32_
         if (e == cudaSuccess)
             e = cudaEventCreateWithFlags(&s->tick_done, cudaEventDisableTiming);
         if (e == cudaSuccess)
+            e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
             e = cudaDeviceSynchronize();
         if (e != cudaSuccess)
             st = scuda(s, e, "mmr_serve_create: set-up");
@@ -618,27 +681,30 @@ mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int
     v.background = background;
     v.pos_bytes = padded_point_bytes(private_n, s->dtype);
     v.bytes = v.pos_bytes + npx * 20;
-    if (s->budget && s->held + v.bytes > s->budget)   // refuse before touching the allocator
+    const uint64_t in_use = s->held - s->cached;      // cached buffers can always be given up
+    if (s->budget && in_use + v.bytes > s->budget)   // refuse before touching the allocator
         return sfail(s, MMR_ERR_BUDGET, "mmr_serve_add_viewer: %llu bytes would exceed the budget (%llu of %llu "
-                     "held)", (unsigned long long)v.bytes, (unsigned long long)s->held,
+                     "in use)", (unsigned long long)v.bytes, (unsigned long long)in_use,
                      (unsigned long long)s->budget);
-    mmr_status st = salloc(s, &v.pos, v.pos_bytes, "private cloud");
+    mmr_status st = vtake(s, &v.pos, v.pos_bytes, &v.cap_pos, "private cloud");
     if (st == MMR_OK)
-        st = salloc(s, (void **)&v.keys[0], npx * 8, "viewer depth-id buffer 0");
+        st = vtake(s, (void **)&v.keys[0], npx * 8, &v.cap_keys[0], "viewer depth-id buffer 0");
     if (st == MMR_OK)
-        st = salloc(s, (void **)&v.keys[1], npx * 8, "viewer depth-id buffer 1");
+        st = vtake(s, (void **)&v.keys[1], npx * 8, &v.cap_keys[1], "viewer depth-id buffer 1");
     if (st == MMR_OK)
-        st = salloc(s, (void **)&v.rgba, npx * 4, "viewer framebuffer");
+        st = vtake(s, (void **)&v.rgba, npx * 4, &v.cap_rgba, "viewer framebuffer");
     if (st == MMR_OK) {
-        cudaError_t e = cudaMemset(v.pos, 0, v.pos_bytes);
+        // The buffers are new or come from a viewer whose last tick has finished, so clearing them on the
+        // engine's own stream needs no wait for the tick in flight; the call returns once they are clear.
+        cudaError_t e = cudaMemsetAsync(v.pos, 0, v.pos_bytes, s->aux);
         if (e == cudaSuccess)
-            e = cudaMemset(v.keys[0], 0xff, npx * 8);
+            e = cudaMemsetAsync(v.keys[0], 0xff, npx * 8, s->aux);
         if (e == cudaSuccess)
-            e = cudaMemset(v.keys[1], 0xff, npx * 8);
+            e = cudaMemsetAsync(v.keys[1], 0xff, npx * 8, s->aux);
         if (e == cudaSuccess)
-            e = cudaMemset(v.rgba, 0, npx * 4);
+            e = cudaMemsetAsync(v.rgba, 0, npx * 4, s->aux);
         if (e == cudaSuccess)
-            e = cudaDeviceSynchronize();
+            e = cudaStreamSynchronize(s->aux);
         if (e != cudaSuccess)
             st = scuda(s, e, "mmr_serve_add_viewer: clearing");
     }

@@ -258,3 +258,52 @@ def test_serve_full_size_sampled():
                                f"gpu {[hex(int(x)) for x in gkeys[bad[:4]]]}, oracle {[hex(int(x)) for x in keys[bad[:4]]]}")
         assert np.array_equal(grgba, rgba), f"rgba of viewer {v} ({W}x{H})"
         assert (keys != oracle.EMPTY_KEY).sum() > W * H // 20
+
+
+def _oracle_viewer_frame(v, n, W, H, shared_ticks, private_steps, eye):
+    shared = _shared()
+    for t in range(shared_ticks):
+        oracle.displace_f32(shared, SHARED_SEED, 0, t, AMP)
+    priv = _private(v, n)
+    for s in range(private_steps):
+        oracle.displace_f32(priv, 3000 + v, 1 + v, s, AMP)
+    both = np.concatenate([shared, priv])
+    colors = np.concatenate([np.full(SHARED_N, SHARED_COLOR, np.uint32), np.full(n, 0xFF000000 | v, np.uint32)])
+    M = oracle.camera_f32(eye, CEN, UP, 60.0, W / H, 0.1, 100.0)
+    return oracle.render(both, "f32", M, W, H, np.float32(0.1), np.float32(100.0), colors, 0, 0x10 + v)
+
+
+def test_serve_reuses_departed_viewers_buffers():
+    """A departed viewer's buffers serve the next join: a join of the same
+    frame size takes no new device memory and still renders like the oracle
+    (its reused buffers were cleared), and a join that needs larger buffers
+    makes the kept ones give way under a budget that holds one viewer."""
+    shared_bytes = (SHARED_N * 12 + 47) // 48 * 48
+    budget = shared_bytes + (1000 * 12 + 47) // 48 * 48 + 64 * 64 * 20 + 100
+    with Server(SHARED_N, "f32", SHARED_SEED, 0, float(AMP), budget_bytes=budget) as srv:
+        srv.shared_points().copy_(torch.from_numpy(_shared()))
+        srv.set_shared_color(SHARED_COLOR)
+
+        def join_and_tick(v, n, W, H):
+            vid = srv.add_viewer(**_viewer_args(v, n, W, H))
+            srv.viewer_points(vid).copy_(torch.from_numpy(_private(v, n)))
+            srv.set_camera(vid, _eye(v, 0), CEN, UP, 60.0, 0.1, 100.0)
+            srv.tick()
+            torch.cuda.synchronize()
+            rgba, keys, f = srv.frame(vid)
+            assert f == 1
+            return vid, keys.cpu().numpy().reshape(-1).view(np.uint64), rgba.cpu().numpy().reshape(-1).view(np.uint32)
+
+        a, _, _ = join_and_tick(0, 1000, 64, 64)                 # tick 0
+        held = srv.status()["device_bytes"]
+        srv.remove_viewer(a)
+        assert srv.status()["device_bytes"] == held and srv.status()["active"] == 0
+        b, keys, rgba = join_and_tick(1, 800, 64, 64)            # tick 1: reused buffers
+        assert srv.status()["device_bytes"] == held
+        want = _oracle_viewer_frame(1, 800, 64, 64, 2, 1, _eye(1, 0))
+        assert np.array_equal(keys, want[0]) and np.array_equal(rgba, want[1])
+        srv.remove_viewer(b)
+        c, keys, rgba = join_and_tick(2, 1000, 4097, 1)          # tick 2: needs larger buffers
+        assert srv.status()["device_bytes"] <= budget and srv.status()["active"] == 1
+        want = _oracle_viewer_frame(2, 1000, 4097, 1, 3, 1, _eye(2, 0))
+        assert np.array_equal(keys, want[0]) and np.array_equal(rgba, want[1])
