@@ -80,6 +80,10 @@ def test_budget_state_and_argument_errors():
             ctx.alloc_points(1_000_000, "f32")
         with pytest.raises(MmrError, match="STATE"):
             ctx.step_and_render()                         # no points yet
+        with pytest.raises(MmrError, match="INVALID"):
+            ctx.alloc_points(0, "f32")                    # an empty cloud is refused, nothing allocated
+        with pytest.raises(MmrError, match="INVALID"):
+            ctx.alloc_points(1 << 32, "f32")              # ids are 32-bit
         ctx.alloc_points(10, "f32")
         with pytest.raises(MmrError, match="STATE"):
             ctx.alloc_points(10, "f32")                   # one point buffer per context
