@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "mmr_device.cuh"
+#include "mmr_disc.cuh"
 #include "mmr_internal.h"
 #include "mmr_points.cuh"
 #include "mmr_resolve.cuh"
