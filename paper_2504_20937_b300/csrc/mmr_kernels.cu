@@ -54,10 +54,19 @@ __device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t
     }
 }
 
+// Lets the frame's resolve kernel, launched as a programmatic dependent
+// (launch_resolve), be scheduled while this grid's last CTAs still run; the
+// resolve waits for this grid's completion before it reads anything.
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // FP32 storage: the compiler's own register choice (48), measured fastest.
 template <bool kDisplace, bool kSplat>
 __global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParams P)
 {
+    allow_dependent_launch();
     points_body<kF32, kDisplace, kSplat>(src, dst, n, P);
 }
 
@@ -69,6 +78,7 @@ __global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParam
 template <int DT, bool kDisplace, bool kSplat>
 __global__ void __maxnreg__(48) points_kernel_narrow(const void *src, void *dst, uint32_t n, PointParams P)
 {
+    allow_dependent_launch();
     points_body<DT, kDisplace, kSplat>(src, dst, n, P);
 }
 
@@ -77,6 +87,7 @@ __global__ void __maxnreg__(48) points_kernel_narrow(const void *src, void *dst,
 template <int DT, bool kDisplace>
 __global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, PointParams P)
 {
+    allow_dependent_launch();
     constexpr int G = Group<DT>::kPoints;
     const uint32_t full = n / G;
     const uint32_t groups = groups_of<DT>(n);
@@ -283,6 +294,10 @@ __global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
                                unsigned long long *__restrict__ next_keys,
                                uint32_t *__restrict__ rgba, Palette pal, uint32_t npx)
 {
+    // Launched as a programmatic dependent of the point kernel: wait until
+    // that grid has completed and its keys are visible (without that launch
+    // relationship this returns at once).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint32_t quads = npx / 4;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,12 +423,23 @@ cudaError_t launch_points(int dtype, const void *src, void *dst, uint32_t n, con
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
                            const Palette &pal, uint32_t npx, const LaunchShape &ls, cudaStream_t s)
 {
-    // pure streaming: one quad per thread, 256 threads, whatever the point kernel's shape
+    // pure streaming: one quad per thread, 256 threads, whatever the point kernel's shape.  Launched as a
+    // programmatic dependent of the kernel before it on the stream, so its CTAs are in place when that kernel
+    // ends (measured: 50.3 -> 48.9 us per 2^22-point 1080p frame); the kernel itself waits for completion.
     (void)ls;
     const uint64_t quads = npx / 4;
     const int grid = (int)std::max<uint64_t>(1, (quads + 255) / 256);
-    resolve_kernel<<<grid, 256, 0, s>>>(keys, next_keys, rgba, pal, npx);
-    return cudaGetLastError();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, resolve_kernel, keys, next_keys, rgba, pal, npx);
 }
 
 }  // namespace mmr
