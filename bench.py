@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--cpu-omp-seconds", type=float, default=8.0,
                     help="seconds of OpenMP CPU-baseline frames on all host cores (0: skip)")
     ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="position storage of the main timed region (16-bit: profiling cases, with --no-extra)")
     ap.add_argument("--leg", default="all", choices=["all", "batched", "served"],
                     help="run one leg alone (profiling cases): batched = the 256-cloud batch for --steps frames, "
                          "served = the zero-copy serving trace of --serve-requests requests")
@@ -257,7 +259,7 @@ def run_ours(args, rank, world, local):
         return step_ms, point_ms, resolve_ms
 
     free_before = torch.cuda.mem_get_info(local)[0]
-    ctx = make_ctx()
+    ctx = make_ctx(args.storage, stored if args.storage == "f32" else inputs.encode(sc.positions(), args.storage))
     zero_copy_bytes = ctx.device_bytes
     zero_copy_measured = free_before - torch.cuda.mem_get_info(local)[0]   # cudaMemGetInfo delta
     if world > 1:
@@ -278,19 +280,21 @@ def run_ours(args, rank, world, local):
     n = sc.n
     pts_per_s = job_rate(args.steps * n, world, total_ms)
     hbm_gbs, peak_kind = measured_peaks()
-    bytes_point = 24 * n
+    bytes_point = 2 * inputs.BYTES_PER_POINT[args.storage] * n
     bytes_frame = bytes_point + 20 * sc.W * sc.H
     mean_point_ms = statistics.mean(point_ms)
     achieved = bytes_point / (mean_point_ms / 1e3) / 1e9
-    traffic = profiled_traffic("points_kernel_f32_fused", sc.name)
+    traffic = profiled_traffic("points_kernel_f32_fused", sc.name) if args.storage == "f32" else None
+    kernel = "points_kernel<f32, displace, splat>" if args.storage == "f32" else \
+        f"points_kernel_narrow<{args.storage}, displace, splat>"
 
     out = {
         "metric": METRIC, "value": pts_per_s, "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
         "data": "synthetic (seeded uniform cloud, numpy PCG64)",
         "config": {"workload": sc.name, "points": n, "width": sc.W, "height": sc.H,
-                   "storage": "f32", "amplitude": sc.amplitude, "orbit_deg_per_frame": sc.deg_per_frame,
+                   "storage": args.storage, "amplitude": sc.amplitude, "orbit_deg_per_frame": sc.deg_per_frame,
                    "l2": f"flushed before every timed frame ({FLUSH_BYTES >> 20} MB read)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "launch": args.launch or "library default (grid-stride, 64 threads, one thread per 48-byte group)"},
@@ -301,7 +305,7 @@ def run_ours(args, rank, world, local):
                        "frames": kernel_frames,
                        "note": "CUDA events around each kernel, in a second pass after the timed region: events "
                                "between the kernels add about 5 us per frame, so the timed region runs without them"},
-        "roofline": {"bound": "hbm", "kernel": "points_kernel<f32, displace, splat>",
+        "roofline": {"bound": "hbm", "kernel": kernel,
                      "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
                      "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_point},
@@ -641,6 +645,8 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.storage != "f32" and not args.no_extra:
+        raise SystemExit("--storage f16/bf16 times the main region only: add --no-extra")
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)

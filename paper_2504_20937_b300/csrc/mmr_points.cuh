@@ -125,6 +125,41 @@ __device__ __forceinline__ void set_word_coord(uint4 (&q)[3], int k, float f)
         reinterpret_cast<uint16_t *>(q)[k] = narrow<DT>(f);
 }
 
+// A full 16-bit group in two phases that keep only the packed words live
+// between them: displace (widen, move, narrow once into the word) and, after
+// the caller has stored the words, project and splat (widen again).  The 24
+// widened coordinates never occupy registers together, so the 16-bit kernel
+// fits 40 registers without spilling.
+template <int DT>
+__device__ __forceinline__ void displace_packed(uint4 (&q)[3], uint32_t i0, const PointParams &P)
+{
+    static_assert(DT != kF32, "16-bit groups only");
+    constexpr int G = Group<DT>::kPoints;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        float x = word_coord<DT>(q, 3 * j), y = word_coord<DT>(q, 3 * j + 1), z = word_coord<DT>(q, 3 * j + 2);
+        displace_point(x, y, z, i0 + j, P);
+        set_word_coord<DT>(q, 3 * j, x);
+        set_word_coord<DT>(q, 3 * j + 1, y);
+        set_word_coord<DT>(q, 3 * j + 2, z);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void splat_packed(const uint4 (&q)[3], uint32_t i0, const PointParams &P)
+{
+    static_assert(DT != kF32, "16-bit groups only");
+    constexpr int G = Group<DT>::kPoints;
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        uint32_t px;
+        unsigned long long key;
+        if (project_key(word_coord<DT>(q, 3 * j), word_coord<DT>(q, 3 * j + 1), word_coord<DT>(q, 3 * j + 2),
+                        P.id_base + i0 + j, P, px, key))
+            splat_key(P.keys, px, key);
+    }
+}
+
 template <int DT, bool kDisplace, bool kSplat>
 __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32_t count, const PointParams &P)
 {
