@@ -72,7 +72,7 @@ def test_launch_shape_does_not_change_results(launch):
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
-@pytest.mark.parametrize("launch", [(256, 4, 0), (256, 2, 1), (128, 8, 1)])
+@pytest.mark.parametrize("launch", [(32, 0, 0), (1024, 0, 0), (256, 4, 0), (256, 2, 1), (128, 8, 1)])
 def test_launch_shapes_16bit(launch, dtype):
     n = 33_333
     stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 27, components=4, sigma=0.05), dtype)
