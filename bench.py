@@ -270,6 +270,11 @@ def run_ours(args, rank, world, local):
         step_ms, _, _ = timed_frames(ctx, sc, args.steps, args.warmup, True)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        # four more repeats of the same K frames: the spread between repeats (`value` is the first)
+        repeat_ms = [sum(step_ms) / args.steps]
+        for _ in range(4):
+            r_ms, _, _ = timed_frames(ctx, sc, args.steps, 0, True)
+            repeat_ms.append(sum(r_ms) / args.steps)
         # the per-kernel durations: a second pass of the same frames with the library's events between the
         # kernels, still under the clock sampler (stopping it perturbs the next few hundred milliseconds)
         kernel_frames = min(args.steps, 200)
@@ -300,6 +305,9 @@ def run_ours(args, rank, world, local):
                    "launch": args.launch or "library default (grid-stride, 64 threads, one thread per 48-byte group)"},
         "frames_per_s": job_rate(args.steps, world, total_ms),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "repeats": {"ms_per_step": repeat_ms, "median_ms_per_step": float(np.median(repeat_ms)),
+                    "note": "the timed region and four more runs of the same K frames, each L2-flushed frame "
+                            "timed the same way; value is the first"},
         "hbm_gbs_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9,
         "kernels_ms": {"points_fused": mean_point_ms, "resolve": statistics.mean(resolve_ms),
                        "frames": kernel_frames,
