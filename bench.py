@@ -570,7 +570,7 @@ def run_batched(hbm_gbs, frames=100):
             "p99_ms": float(np.percentile(frame_ms, 99)), "points_per_s": n_pts / (ms / 1e3),
             "cloud_frames_per_s": len(clouds) / (ms / 1e3),
             "hbm_gbs_frame": bytes_frame / (ms / 1e3) / 1e9, "frac_frame": bytes_frame / (ms / 1e3) / 1e9 / hbm_gbs,
-            "launch": "one persistent point launch + one persistent resolve launch + counter, replayed as a CUDA graph"}
+            "launch": "counter resets + one persistent launch (point items, then each cloud's pixel items one resident grid later) + frame counter, replayed as a CUDA graph"}
 
 
 def run_served(requests=10_000, roundtrip=True):

@@ -251,14 +251,18 @@ MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
 
 /* ---- batched clouds --------------------------------------------------------
  * Many independent clouds, each with its own size, framebuffer, camera and
- * displacement parameters, advanced and rendered together: one persistent
- * launch of the point kernel covers every cloud's points and one of the
- * resolve kernel covers every cloud's pixels.  A device-side frame counter
- * picks the Philox step, the camera slot and the depth-id buffer, so one
- * captured frame can be replayed as a CUDA graph with nothing changed on
- * the host.  Each cloud's result is identical to rendering it alone in its
- * own mmr_ctx with the same parameters (the per-pixel minimum does not
- * depend on launch order). */
+ * displacement parameters, advanced and rendered together by one persistent
+ * launch per frame.  Its CTAs take work items from one list: each cloud's
+ * point items (displace, project, splat), and that cloud's pixel items
+ * (resolve, clear) placed about one resident grid later, so that its
+ * depth-id buffer is normally still in L2 when it is resolved.  A pixel item
+ * waits, bounded, until its cloud's point items are done; a wait that gives
+ * up raises the batch's device error flag (mmr_batch_check_device).  A
+ * device-side frame counter picks the Philox step, the camera slot and the
+ * depth-id buffer, so one captured frame can be replayed as a CUDA graph
+ * with nothing changed on the host.  Each cloud's result is identical to
+ * rendering it alone in its own mmr_ctx with the same parameters (the
+ * per-pixel minimum does not depend on the order of the work). */
 typedef struct mmr_batch mmr_batch;
 
 typedef struct mmr_cloud_desc {
@@ -293,13 +297,16 @@ MMR_API mmr_status mmr_batch_set_camera(mmr_batch *b, int cloud, int slot, const
                                         double znear, double zfar);
 
 /* Launch shape: threads per block (multiple of 32, 32..512), CTAs per SM
- * of the persistent grid (0 = one CTA per chunk), and point groups per chunk
- * (1..65536; a group is 48 bytes of positions).  Results never depend on it. */
+ * of the persistent grid (0 = as many as fit), and point groups per item
+ * (1..65536; a group is 48 bytes of positions; a pixel item covers 16 pixels
+ * per group).  Rebuilds the work list (synchronises the device).  Results
+ * never depend on it. */
 MMR_API mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_sm, int chunk_groups);
 
-/* One frame of every cloud: displace + project + splat (one launch), then
- * resolve + clear (one launch), then advance the device frame counter.
- * Requires every cloud's camera for the slot the frame uses. */
+/* One frame of every cloud: displace + project + splat and resolve + clear
+ * (one launch, after resetting the work counters), then advance the device
+ * frame counter.  Requires every cloud's camera for the slot the frame
+ * uses. */
 MMR_API mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream);
 
 /* `frames` frames by replaying a CUDA graph of one frame (captured on first
@@ -316,6 +323,19 @@ MMR_API mmr_status mmr_batch_run_graph(mmr_batch *b, int frames, void *stream);
  * the positions (counted against the budget). */
 MMR_API mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config, int *threads,
                                       int *ctas_per_sm, int *chunk_groups, float *best_ms);
+
+/* Synchronise the device and report whether a pixel item of this batch gave
+ * up its bounded wait (MMR_ERR_TIMEOUT; the flag is then cleared) since the
+ * last check.  That frame is incomplete; the batch stays usable. */
+MMR_API mmr_status mmr_batch_check_device(mmr_batch *b);
+
+/* Failure-path self-test: one thread runs the pixel items' wait on a count
+ * that nothing ever decrements, gives up after max_polls polls (1..2^24,
+ * about 64 ns apart) and raises the batch's device error flag, as a pixel
+ * item whose cloud's point items never finished would.  Enqueued on
+ * `stream`; mmr_batch_check_device then reports MMR_ERR_TIMEOUT.  No fault
+ * and no unbounded wait is involved. */
+MMR_API mmr_status mmr_batch_selftest_bounded_wait(mmr_batch *b, uint32_t max_polls, void *stream);
 
 /* Latest frame of one cloud (device pointers, as mmr_frame_ptr). */
 MMR_API mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t **rgba,

@@ -284,6 +284,14 @@ class Batch:
                                                  C.byref(c), C.byref(g), C.byref(ms)))
         return {"threads": t.value, "ctas_per_sm": c.value, "chunk_groups": g.value, "ms_per_frame": ms.value}
 
+    def check_device(self):
+        """Raise MmrError(MMR_ERR_TIMEOUT) if a pixel item gave up its bounded wait."""
+        self._check(self._lib.mmr_batch_check_device(self._h))
+
+    def selftest_bounded_wait(self, max_polls: int = 1000, stream=None):
+        """Run the pixel items' bounded wait on a count that never reaches zero (see include/mmr.h)."""
+        self._check(self._lib.mmr_batch_selftest_bounded_wait(self._h, max_polls, stream_handle(stream)))
+
     def frame_rgba(self, i: int) -> torch.Tensor:
         r, k = C.c_void_p(), C.c_void_p()
         self._check(self._lib.mmr_batch_frame_ptr(self._h, i, C.byref(r), C.byref(k)))

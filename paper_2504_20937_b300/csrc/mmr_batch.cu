@@ -1,15 +1,22 @@
 // Batched clouds (include/mmr.h, mmr_batch_*): many independent clouds of
 // uneven size, each with its own camera and framebuffer, advanced and
-// rendered by one persistent point launch and one persistent resolve launch
-// per frame.
+// rendered by one persistent launch per frame.
 //
-// Work is cut into chunks: a point chunk is up to `chunk_groups` 48-byte
-// point groups of one cloud, a pixel chunk up to 4*chunk_groups quads of one
-// cloud's framebuffer.  A persistent CTA strides over the chunk table, so a
-// 1e3-point cloud and a 1e6-point cloud cost in proportion to their size and
-// no CTA idles on a small cloud.  A device-side frame counter selects the
-// Philox step, the camera slot and the depth-id buffer, so a captured frame
-// replays as a CUDA graph with no host update.
+// Work is cut into items: a point item is up to `chunk_groups` 48-byte point
+// groups of one cloud (displace, project, splat), a pixel item up to
+// 4*chunk_groups quads of one cloud's framebuffer (resolve, clear the other
+// depth-id buffer).  Persistent CTAs take items in list order from one
+// counter, so a 1e3-point cloud and a 1e6-point cloud cost in proportion to
+// their size and no CTA idles on a small cloud.  The list holds every
+// cloud's point items in order, and a cloud's pixel items once about one
+// resident grid's worth of later point items precede them: by the time they
+// are taken the cloud's points are normally done and its depth-id buffer is
+// still in L2, so the resolve reads it from there rather than from DRAM.  A
+// pixel item waits (bounded) for its cloud's count of unfinished point items
+// to reach zero; every point item it waits on was taken earlier by a running
+// CTA and never waits itself, so the wait ends.  A device-side frame counter
+// selects the Philox step, the camera slot and the depth-id buffer, so a
+// captured frame replays as a CUDA graph with no host update.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -42,96 +49,163 @@ struct CloudDev {
     uint32_t color, background;
 };
 
+// Item word x: the cloud, with this bit set for a pixel item; y: the first
+// point group (point item) or quad (pixel item).
+constexpr uint32_t kPixelItem = 0x80000000u;
+
 struct BatchTables {
     const CloudDev *clouds;
     const Cam *cams;            // [slots][count]
-    const uint2 *point_chunks;  // (cloud, first group)
-    const uint2 *pixel_chunks;  // (cloud, first quad)
-    uint32_t n_point_chunks;
-    uint32_t n_pixel_chunks;
+    const uint2 *items;         // hand-out order
+    uint32_t n_items;
     uint32_t chunk_groups;
     uint32_t chunk_quads;
     uint32_t count;
     uint32_t slots;
     uint32_t first_step;
+    uint32_t spin_limit;        // polls before a pixel item gives up waiting
     uint32_t *frame;            // device frame counter
+    uint32_t *next;             // next item to hand out, zeroed before every frame
+    uint32_t *remaining;        // [count] unfinished point items per cloud, reset before every frame
+    uint32_t *err;              // bit 0: a bounded wait gave up
 };
+
+// Bounded wait until *count reads 0 (acquire, GPU scope), polling about
+// every 64 ns at most `limit` times; on giving up sets bit 0 of *err and
+// returns false.
+__device__ __forceinline__ bool wait_until_zero(const uint32_t *count, uint32_t limit, uint32_t *err)
+{
+    for (uint32_t k = 0;; ++k) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+        if (v == 0)
+            return true;
+        if (k >= limit) {
+            atomicOr(err, 1u);
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
 
 // At most 512 threads per block (a bound the autotuner stays well below).
 constexpr int kBatchMaxThreads = 512;
 
-// One chunk's cloud parameters are built once per CTA in shared memory and
-// read from there by every thread: held in registers by each thread they
-// cost some 30 registers and halve the resident warps.
+// Resolve + clear of four pixels with the keys read from L2 (ld.global.cg):
+// this SM's L1 may still hold lines of this cloud's keys from its own early
+// depth tests, older than the atomics that followed.
+__device__ __forceinline__ void resolve_quad_l2(const unsigned long long *keys, unsigned long long *next_keys,
+                                                uint32_t *rgba, const Palette &pal, uint32_t q)
+{
+    const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q);
+    const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q + 1);
+    const uint4 c = make_uint4(key_colour(k01.x, pal), key_colour(k01.y, pal), key_colour(k23.x, pal),
+                               key_colour(k23.y, pal));
+    __stcs(reinterpret_cast<uint4 *>(rgba) + q, c);
+    const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
+    reinterpret_cast<ulonglong2 *>(next_keys)[2 * q] = e;
+    reinterpret_cast<ulonglong2 *>(next_keys)[2 * q + 1] = e;
+}
+
+// One frame of every cloud.  A point item's cloud parameters are built once
+// per CTA in shared memory and read from there by every thread: held in
+// registers by each thread they cost some 30 registers and halve the
+// resident warps.
 template <int DT>
-__global__ void __launch_bounds__(kBatchMaxThreads) batch_points_kernel(BatchTables T)
+__global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTables T)
 {
     constexpr uint32_t G = Group<DT>::kPoints;
     __shared__ PointParams sP;
-    __shared__ uint32_t s_n;
+    __shared__ uint32_t s_n, s_item, s_ok;
     __shared__ void *s_pos;
     const uint32_t frame = *T.frame;
     const uint32_t slot = frame % T.slots;
     const int buf = frame & 1;
-    for (uint32_t c = blockIdx.x; c < T.n_point_chunks; c += gridDim.x) {
-        const uint2 ch = T.point_chunks[c];
-        if (threadIdx.x == 0) {
-            const CloudDev &cl = T.clouds[ch.x];
-            PointParams P;
-            P.cam = T.cams[(size_t)slot * T.count + ch.x];
-            P.keys = cl.keys[buf];
-            P.W = cl.W;
-            P.H = cl.H;
-            P.fW = cl.fW;
-            P.fH = cl.fH;
-            P.halfW = cl.halfW;
-            P.halfH = cl.halfH;
-            P.seed_lo = cl.seed_lo;
-            P.seed_hi = cl.seed_hi;
-            P.step = T.first_step + frame;
-            P.cloud = cl.cloud;
-            P.amplitude = cl.amplitude;
-            P.id_base = 0;
-            philox_prepare(P);
-            sP = P;
-            s_n = cl.n;
-            s_pos = cl.pos;
-        }
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(T.next, 1u);
         __syncthreads();
-        const uint32_t n = s_n;
-        void *pos = s_pos;
-        const uint32_t full = n / G;
-        const uint32_t end = min(ch.y + T.chunk_groups, groups_of<DT>(n));
-        for (uint32_t g = ch.y + threadIdx.x; g < end; g += blockDim.x) {
-            if (g < full) {
-                uint4 q[3];
-                load_words(pos, g, q);
-                process_words<DT, true, true>(q, g * G, G, sP);
-                store_words(pos, g, q);
-            } else {
-                process_tail<DT, true, true>(pos, pos, n, g * G, sP);
+        const uint32_t it = s_item;
+        if (it >= T.n_items)
+            break;
+        const uint2 w = T.items[it];
+        const uint32_t cloud = w.x & ~kPixelItem;
+        if (w.x & kPixelItem) {
+            if (threadIdx.x == 0) {
+                s_ok = wait_until_zero(T.remaining + cloud, T.spin_limit, T.err);
+                __threadfence();
+            }
+            __syncthreads();
+            if (s_ok) {
+                const CloudDev &cl = T.clouds[cloud];
+                const unsigned long long *keys = cl.keys[buf];
+                unsigned long long *nk = cl.keys[buf ^ 1];
+                const uint32_t quads = cl.npx / 4;
+                const uint32_t end = min(w.y + T.chunk_quads, quads);
+                const Palette pal{nullptr, nullptr, nullptr, 0u, cl.color, cl.background};
+                for (uint32_t q = w.y + threadIdx.x; q < end; q += blockDim.x)
+                    resolve_quad_l2(keys, nk, cl.rgba, pal, q);
+                if (end == quads && quads * 4 + threadIdx.x < cl.npx) {     // the ragged tail
+                    const uint32_t p = quads * 4 + threadIdx.x;
+                    cl.rgba[p] = key_colour(__ldcg(keys + p), pal);
+                    nk[p] = kEmptyKey;
+                }
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                const CloudDev &cl = T.clouds[cloud];
+                PointParams P;
+                P.cam = T.cams[(size_t)slot * T.count + cloud];
+                P.keys = cl.keys[buf];
+                P.W = cl.W;
+                P.H = cl.H;
+                P.fW = cl.fW;
+                P.fH = cl.fH;
+                P.halfW = cl.halfW;
+                P.halfH = cl.halfH;
+                P.seed_lo = cl.seed_lo;
+                P.seed_hi = cl.seed_hi;
+                P.step = T.first_step + frame;
+                P.cloud = cl.cloud;
+                P.amplitude = cl.amplitude;
+                P.id_base = 0;
+                philox_prepare(P);
+                sP = P;
+                s_n = cl.n;
+                s_pos = cl.pos;
+            }
+            __syncthreads();
+            const uint32_t n = s_n;
+            void *pos = s_pos;
+            const uint32_t full = n / G;
+            const uint32_t end = min(w.y + T.chunk_groups, groups_of<DT>(n));
+            for (uint32_t g = w.y + threadIdx.x; g < end; g += blockDim.x) {
+                if (g < full) {
+                    uint4 q[3];
+                    load_words(pos, g, q);
+                    process_words<DT, true, true>(q, g * G, G, sP);
+                    store_words(pos, g, q);
+                } else {
+                    process_tail<DT, true, true>(pos, pos, n, g * G, sP);
+                }
+            }
+            __threadfence();            // this thread's atomics and stores, before the count below
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicSub(T.remaining + cloud, 1u);
             }
         }
-        __syncthreads();            // sP is rewritten for the next chunk
+        __syncthreads();                // s_item, s_ok and sP are rewritten for the next item
     }
 }
 
-__global__ void batch_resolve_kernel(BatchTables T)
+// Failure-path self-test of the pixel items' wait: one thread waits on a
+// count that nothing decrements and gives up after `limit` polls.
+__global__ void batch_wait_selftest_kernel(const uint32_t *never_zero, uint32_t limit, uint32_t *err)
 {
-    const int buf = *T.frame & 1;
-    for (uint32_t c = blockIdx.x; c < T.n_pixel_chunks; c += gridDim.x) {
-        const uint2 ch = T.pixel_chunks[c];
-        const CloudDev &cl = T.clouds[ch.x];
-        const unsigned long long *keys = cl.keys[buf];
-        unsigned long long *next = cl.keys[buf ^ 1];
-        const uint32_t quads = cl.npx / 4;
-        const uint32_t end = min(ch.y + T.chunk_quads, quads);
-        const Palette pal{nullptr, nullptr, nullptr, 0u, cl.color, cl.background};
-        for (uint32_t q = ch.y + threadIdx.x; q < end; q += blockDim.x)
-            resolve_quad(keys, next, cl.rgba, pal, q);
-        if (end == quads && quads * 4 + threadIdx.x < cl.npx)
-            resolve_pixel(keys, next, cl.rgba, pal, quads * 4 + threadIdx.x);
-    }
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        wait_until_zero(never_zero, limit, err);
 }
 
 __global__ void batch_advance_kernel(uint32_t *frame) { *frame += 1u; }
@@ -159,11 +233,13 @@ struct mmr_batch {
     uint32_t *rgba_base = nullptr;
     mmr::CloudDev *d_clouds = nullptr;
     mmr::Cam *d_cams = nullptr;
-    uint2 *d_point_chunks = nullptr;
-    uint2 *d_pixel_chunks = nullptr;
-    uint64_t point_chunk_bytes = 0, pixel_chunk_bytes = 0;
-    uint32_t n_point_chunks = 0, n_pixel_chunks = 0;
+    uint2 *d_items = nullptr;        // work list in hand-out order
+    uint64_t item_bytes = 0;
+    uint32_t n_items = 0;
+    int grid = 1;                    // resident CTAs of the persistent launch
     uint32_t *d_frame = nullptr;
+    uint32_t *d_work = nullptr;      // [0] next item, [1] error bits, [2] self-test count (never zero)
+    uint32_t *d_remaining = nullptr; // [count] unfinished point items per cloud, then [count] their full counts
 
     std::vector<mmr::Cam> cams;      // host copy [slots][count]
     std::vector<uint8_t> cam_set;
@@ -233,56 +309,111 @@ uint32_t groups_for(uint64_t n, int dtype)
 
 uint32_t chunk_quads(const mmr_batch *b) { return 4u * b->chunk_groups; }
 
-// (Re)build the point and pixel chunk tables for the current chunk size.
-mmr_status build_chunks(mmr_batch *b)
+// Resident CTAs of the persistent launch for the current shape: CTAs per SM
+// as set, or as many as fit (0).
+cudaError_t resident_grid(const mmr_batch *b, int *grid)
 {
-    std::vector<uint2> pc, xc;
+    int per_sm = b->launch.ctas_per_sm;
+    if (per_sm <= 0) {
+        cudaError_t e;
+        switch (b->dtype) {
+        case MMR_F32x3:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kF32>,
+                                                              b->launch.threads, 0);
+            break;
+        case MMR_F16x3:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kF16>,
+                                                              b->launch.threads, 0);
+            break;
+        default:
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kBF16>,
+                                                              b->launch.threads, 0);
+            break;
+        }
+        if (e != cudaSuccess)
+            return e;
+    }
+    *grid = std::max(1, per_sm) * b->launch.sm_count;
+    return cudaSuccess;
+}
+
+// (Re)build the work list for the current chunk size and launch shape.  A
+// cloud's pixel items follow its last point item once `grid` further point
+// items have been listed: by then the point items taken before them have
+// normally finished (measured on the 256-cloud scene: a lag of 0.5 to 4
+// grids all within 1.5% of the best, 0 to 0.15 grids up to 15% slower, all
+// pixel items at the end 6% slower).
+mmr_status build_items(mmr_batch *b)
+{
+    int grid = 1;
+    cudaError_t e = resident_grid(b, &grid);
+    if (e != cudaSuccess)
+        return bcuda(b, e, "occupancy query");
     const uint32_t cq = chunk_quads(b);
-    for (int c = 0; c < b->count; ++c) {
-        const uint32_t groups = groups_for(b->desc[c].n, b->dtype);
-        for (uint32_t g = 0; g < groups; g += b->chunk_groups)
-            pc.push_back(make_uint2((uint32_t)c, g));
+    std::vector<uint2> items;
+    std::vector<uint32_t> counts(2 * (size_t)b->count, 0);
+    std::vector<std::pair<uint32_t, uint64_t>> done;     // (cloud, point items listed after its last one)
+    uint64_t listed = 0;
+    size_t head = 0;
+    auto push_pixels = [&](uint32_t c) {
         const uint32_t quads = (uint32_t)(((uint64_t)b->desc[c].width * b->desc[c].height) / 4);
         uint32_t q = 0;
-        do {                          // at least one chunk per cloud: it owns the ragged tail
-            xc.push_back(make_uint2((uint32_t)c, q));
+        do {                          // at least one item per cloud: it owns the ragged tail
+            items.push_back(make_uint2(c | mmr::kPixelItem, q));
             q += cq;
         } while (q < quads);
+    };
+    for (int c = 0; c < b->count; ++c) {
+        const uint32_t groups = groups_for(b->desc[c].n, b->dtype);
+        for (uint32_t g = 0; g < groups; g += b->chunk_groups) {
+            items.push_back(make_uint2((uint32_t)c, g));
+            counts[c] += 1;
+            ++listed;
+            while (head < done.size() && listed - done[head].second >= (uint64_t)grid)
+                push_pixels(done[head++].first);
+        }
+        done.push_back({(uint32_t)c, listed});
     }
-    bfree(b, (void **)&b->d_point_chunks, b->point_chunk_bytes);
-    bfree(b, (void **)&b->d_pixel_chunks, b->pixel_chunk_bytes);
-    b->point_chunk_bytes = pc.size() * sizeof(uint2);
-    b->pixel_chunk_bytes = xc.size() * sizeof(uint2);
-    mmr_status st = balloc(b, (void **)&b->d_point_chunks, b->point_chunk_bytes, "point chunk table");
-    if (st == MMR_OK)
-        st = balloc(b, (void **)&b->d_pixel_chunks, b->pixel_chunk_bytes, "pixel chunk table");
+    while (head < done.size())
+        push_pixels(done[head++].first);
+    for (int c = 0; c < b->count; ++c)
+        counts[b->count + c] = counts[c];
+    bfree(b, (void **)&b->d_items, b->item_bytes);
+    b->n_items = 0;                  // until the new list is in place a frame hands out nothing
+    b->item_bytes = items.size() * sizeof(uint2);
+    mmr_status st = balloc(b, (void **)&b->d_items, b->item_bytes, "work list");
     if (st != MMR_OK)
         return st;
-    cudaError_t e = cudaMemcpy(b->d_point_chunks, pc.data(), b->point_chunk_bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(b->d_items, items.data(), b->item_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_pixel_chunks, xc.data(), b->pixel_chunk_bytes, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(b->d_remaining, counts.data(), counts.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
-        return bcuda(b, e, "chunk table upload");
-    b->n_point_chunks = (uint32_t)pc.size();
-    b->n_pixel_chunks = (uint32_t)xc.size();
+        return bcuda(b, e, "work list upload");
+    b->n_items = (uint32_t)items.size();
+    b->grid = grid;
     return MMR_OK;
 }
+
+// Polls before a pixel item gives up waiting (about a second).
+constexpr uint32_t kSpinLimit = 1u << 24;
 
 mmr::BatchTables tables(const mmr_batch *b)
 {
     mmr::BatchTables T;
     T.clouds = b->d_clouds;
     T.cams = b->d_cams;
-    T.point_chunks = b->d_point_chunks;
-    T.pixel_chunks = b->d_pixel_chunks;
-    T.n_point_chunks = b->n_point_chunks;
-    T.n_pixel_chunks = b->n_pixel_chunks;
+    T.items = b->d_items;
+    T.n_items = b->n_items;
     T.chunk_groups = b->chunk_groups;
     T.chunk_quads = chunk_quads(b);
     T.count = (uint32_t)b->count;
     T.slots = (uint32_t)b->slots;
     T.first_step = 0;
+    T.spin_limit = kSpinLimit;
     T.frame = b->d_frame;
+    T.next = b->d_work;
+    T.remaining = b->d_remaining;
+    T.err = b->d_work + 1;
     return T;
 }
 
@@ -303,27 +434,23 @@ mmr_status upload_cameras(mmr_batch *b, cudaStream_t s)
     return MMR_OK;
 }
 
-int grid_for(const mmr_batch *b, uint32_t chunks)
-{
-    if (b->launch.ctas_per_sm > 0)
-        return std::max(1, std::min<int>(b->launch.sm_count * b->launch.ctas_per_sm, (int)std::max(1u, chunks)));
-    return (int)std::max(1u, chunks);
-}
-
-// Enqueue one frame (three kernels) on s; no host synchronisation.
+// Enqueue one frame on s: reset the hand-out counter and the per-cloud
+// counts, one persistent launch, advance the frame counter.  No host
+// synchronisation.
 cudaError_t enqueue_frame(const mmr_batch *b, cudaStream_t s)
 {
     const mmr::BatchTables T = tables(b);
-    const int gp = grid_for(b, b->n_point_chunks);
-    switch (b->dtype) {
-    case MMR_F32x3: mmr::batch_points_kernel<mmr::kF32><<<gp, b->launch.threads, 0, s>>>(T); break;
-    case MMR_F16x3: mmr::batch_points_kernel<mmr::kF16><<<gp, b->launch.threads, 0, s>>>(T); break;
-    default: mmr::batch_points_kernel<mmr::kBF16><<<gp, b->launch.threads, 0, s>>>(T); break;
-    }
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(b->d_work, 0, sizeof(uint32_t), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_remaining, b->d_remaining + b->count, sizeof(uint32_t) * b->count,
+                            cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess)
         return e;
-    mmr::batch_resolve_kernel<<<grid_for(b, b->n_pixel_chunks), b->launch.threads, 0, s>>>(T);
+    switch (b->dtype) {
+    case MMR_F32x3: mmr::batch_frame_kernel<mmr::kF32><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    case MMR_F16x3: mmr::batch_frame_kernel<mmr::kF16><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    default: mmr::batch_frame_kernel<mmr::kBF16><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
@@ -368,9 +495,10 @@ mmr_status mmr_batch_destroy(mmr_batch *b)
     bfree(b, (void **)&b->rgba_base, b->total_px * 4);
     bfree(b, (void **)&b->d_clouds, (uint64_t)b->count * sizeof(mmr::CloudDev));
     bfree(b, (void **)&b->d_cams, b->cams.size() * sizeof(mmr::Cam));
-    bfree(b, (void **)&b->d_point_chunks, b->point_chunk_bytes);
-    bfree(b, (void **)&b->d_pixel_chunks, b->pixel_chunk_bytes);
+    bfree(b, (void **)&b->d_items, b->item_bytes);
     bfree(b, (void **)&b->d_frame, 4);
+    bfree(b, (void **)&b->d_work, 3 * sizeof(uint32_t));
+    bfree(b, (void **)&b->d_remaining, 2 * sizeof(uint32_t) * (uint64_t)b->count);
     if (b->staging)
         cudaFreeHost(b->staging);
     if (b->staging_done)
@@ -442,7 +570,14 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
     if (st == MMR_OK)
         st = balloc(b, (void **)&b->d_frame, 4, "frame counter");
     if (st == MMR_OK)
-        st = build_chunks(b);
+        st = balloc(b, (void **)&b->d_work, 3 * sizeof(uint32_t), "work counters");
+    if (st == MMR_OK)
+        st = balloc(b, (void **)&b->d_remaining, 2 * sizeof(uint32_t) * (uint64_t)count, "per-cloud counts");
+    if (st == MMR_OK) {
+        const uint32_t init[3] = {0u, 0u, 1u};
+        e = cudaMemcpy(b->d_work, init, sizeof init, cudaMemcpyHostToDevice);
+        st = e == cudaSuccess ? build_items(b) : bcuda(b, e, "mmr_batch_create: work counters");
+    }
     if (st == MMR_OK) {
         std::vector<mmr::CloudDev> host(count);
         for (int c = 0; c < count; ++c) {
@@ -540,18 +675,14 @@ mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_sm, int 
     if (threads < 32 || threads > mmr::kBatchMaxThreads || threads % 32 || ctas_per_sm < 0 || ctas_per_sm > 64 ||
         chunk_groups < 1 || chunk_groups > 65536)
         return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_set_launch: out of range");
-    const bool rechunk = (uint32_t)chunk_groups != b->chunk_groups;
     b->launch.threads = threads;
     b->launch.ctas_per_sm = ctas_per_sm;
     b->chunk_groups = (uint32_t)chunk_groups;
     drop_graph(b);
-    if (rechunk) {
-        cudaError_t e = cudaDeviceSynchronize();     // old tables may still be in use
-        if (e != cudaSuccess)
-            return bcuda(b, e, "mmr_batch_set_launch: sync");
-        return build_chunks(b);
-    }
-    return MMR_OK;
+    cudaError_t e = cudaDeviceSynchronize();         // the old work list may still be in use
+    if (e != cudaSuccess)
+        return bcuda(b, e, "mmr_batch_set_launch: sync");
+    return build_items(b);                           // chunk size and resident grid set the list
 }
 
 mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream)
@@ -715,6 +846,33 @@ mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config,
     if (best_ms)
         *best_ms = best;
     return MMR_OK;
+}
+
+mmr_status mmr_batch_check_device(mmr_batch *b)
+{
+    if (!b)
+        return MMR_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    uint32_t err = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&err, b->d_work + 1, sizeof err, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && err)
+        e = cudaMemset(b->d_work + 1, 0, sizeof err);
+    if (e != cudaSuccess)
+        return bcuda(b, e, "mmr_batch_check_device");
+    if (err)
+        return bfail(b, MMR_ERR_TIMEOUT, "mmr_batch_check_device: a pixel item gave up waiting for its cloud's "
+                                         "point items; that frame is incomplete");
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_selftest_bounded_wait(mmr_batch *b, uint32_t max_polls, void *stream)
+{
+    if (!b || max_polls < 1 || max_polls > kSpinLimit)
+        return bfail(b, MMR_ERR_INVALID_ARG, "mmr_batch_selftest_bounded_wait: max_polls must be 1..2^24");
+    mmr::batch_wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(b->d_work + 2, max_polls, b->d_work + 1);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MMR_OK : bcuda(b, e, "mmr_batch_selftest_bounded_wait");
 }
 
 mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t **rgba, const uint64_t **depth_id)

@@ -59,6 +59,7 @@ def _oracle(c, s, eye, dtype, frames):
 
 
 def _check_all(batch, clouds, stored, eyes, dtype, frames):
+    batch.check_device()                    # no pixel item gave up waiting
     for i, c in enumerate(clouds):
         g = _download(batch, i, dtype)
         o = _oracle(c, stored[i], eyes[i], dtype, frames)

@@ -9,6 +9,7 @@ import textwrap
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2504_20937_b300 import inputs
 from paper_2504_20937_b300.api import Context, MmrError
@@ -42,6 +43,28 @@ def _run_child(code, env_extra):
     env = dict(os.environ, **env_extra)
     return subprocess.run([sys.executable, "-c", textwrap.dedent(code)], cwd=ROOT, env=env,
                           capture_output=True, text=True, timeout=300)
+
+
+def test_batch_bounded_wait_times_out_and_batch_stays_usable():
+    """The batch's pixel items wait for their cloud's point items with a
+    bounded poll; run that wait on a count that never reaches zero."""
+    from paper_2504_20937_b300.api import Batch
+    stored = inputs.encode(inputs.uniform_cloud(3000, 32), "f32")
+    desc = dict(n=3000, width=40, height=30, seed=3, cloud=0, amplitude=1e-3)
+    with Batch([desc], "f32") as b:
+        b.check_device()                                 # clean to start with
+        b.selftest_bounded_wait(max_polls=1000)          # ~0.1 ms of polling, the count never reaches zero
+        with pytest.raises(MmrError, match="TIMEOUT"):
+            b.check_device()
+        b.check_device()                                 # the flag was cleared
+        b.points(0).copy_(torch.from_numpy(stored))
+        b.set_camera(0, 0, (0.5, 0.5, 2.5), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)
+        for _ in range(2):
+            b.step_and_render()
+        b.check_device()
+        keys = b.frame_keys(0).cpu().numpy().reshape(-1).view(np.uint64)
+    o = oracle_run(stored, "f32", 40, 30, 3, 1e-3, 2, fixed_eye)
+    assert np.array_equal(keys, o[1])
 
 
 def test_injected_allocation_failures():
