@@ -304,9 +304,9 @@ MMR_API mmr_status mmr_batch_set_camera(mmr_batch *b, int cloud, int slot, const
 MMR_API mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_sm, int chunk_groups);
 
 /* One frame of every cloud: displace + project + splat and resolve + clear
- * (one launch, after resetting the work counters), then advance the device
- * frame counter.  Requires every cloud's camera for the slot the frame
- * uses. */
+ * (one persistent launch, after resetting the work counters and building
+ * every cloud's parameters for the frame), then advance the device frame
+ * counter.  Requires every cloud's camera for the slot the frame uses. */
 MMR_API mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream);
 
 /* `frames` frames by replaying a CUDA graph of one frame (captured on first
