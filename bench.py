@@ -561,6 +561,19 @@ def run_batched(hbm_gbs, frames=100):
         torch.cuda.synchronize()
         total_ms = t0.elapsed_time(t1)
         frame_ms = [a.elapsed_time(z) for a, z in per_frame]
+        # the same frames by the host round trip: displace, all positions device -> pinned host -> device, render
+        rt_frames = max(3, min(frames // 10, 10))
+        b.step_and_render_roundtrip(stream, pinned=True)          # allocates the host and device copies
+        rt_ms = []
+        for f in range(rt_frames):
+            a = torch.cuda.Event(enable_timing=True)
+            z = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.step_and_render_roundtrip(stream, pinned=True)
+            z.record(stream)
+            z.synchronize()
+            rt_ms.append(a.elapsed_time(z))
+        b.check_device()
     n_pts = sum(c["n"] for c in clouds)
     n_px = sum(c["width"] * c["height"] for c in clouds)
     bytes_frame = 24 * n_pts + 20 * n_px
@@ -570,6 +583,11 @@ def run_batched(hbm_gbs, frames=100):
             "p99_ms": float(np.percentile(frame_ms, 99)), "points_per_s": n_pts / (ms / 1e3),
             "cloud_frames_per_s": len(clouds) / (ms / 1e3),
             "hbm_gbs_frame": bytes_frame / (ms / 1e3) / 1e9, "frac_frame": bytes_frame / (ms / 1e3) / 1e9 / hbm_gbs,
+            "roundtrip_pinned": {"ms_per_frame": statistics.mean(rt_ms), "p50_ms": float(np.percentile(rt_ms, 50)),
+                                 "p99_ms": float(np.percentile(rt_ms, 99)), "frames": rt_frames,
+                                 "points_per_s": n_pts / (statistics.mean(rt_ms) / 1e3),
+                                 "host_bytes_per_frame": 2 * 12 * n_pts},
+            "zero_copy_vs_roundtrip": statistics.mean(rt_ms) / ms,
             "launch": "counter resets + one persistent launch (point items, then each cloud's pixel items one resident grid later) + frame counter, replayed as a CUDA graph"}
 
 

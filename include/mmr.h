@@ -309,6 +309,16 @@ MMR_API mmr_status mmr_batch_set_launch(mmr_batch *b, int threads, int ctas_per_
  * counter.  Requires every cloud's camera for the slot the frame uses. */
 MMR_API mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream);
 
+/* The same frame by the paper's RAM-based path, for comparison: displace
+ * every cloud (one persistent launch, no splat), copy all positions device
+ * -> host (pinned when pinned_host != 0, else pageable) -> a second device
+ * buffer, render every cloud from that copy (one persistent launch, no
+ * displacement), advance the frame counter.  Results are identical to
+ * mmr_batch_step_and_render.  The host and device copies (the positions'
+ * size each) are allocated on first use and kept until mmr_batch_destroy;
+ * the device copy counts against the budget.  Enqueued on `stream`. */
+MMR_API mmr_status mmr_batch_step_and_render_roundtrip(mmr_batch *b, void *stream, int pinned_host);
+
 /* `frames` frames by replaying a CUDA graph of one frame (captured on first
  * use and again after mmr_batch_set_launch).  Same results as calling
  * mmr_batch_step_and_render `frames` times. */

@@ -85,6 +85,7 @@ SIGNATURES.update({
     "mmr_batch_frame_ptr": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp)]),
     "mmr_batch_frames": (_i, [_vp, C.POINTER(_u32)]),
     "mmr_batch_check_device": (_i, [_vp]),
+    "mmr_batch_step_and_render_roundtrip": (_i, [_vp, _vp, _i]),
     "mmr_batch_selftest_bounded_wait": (_i, [_vp, _u32, _vp]),
     "mmr_batch_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
 })

@@ -275,6 +275,10 @@ class Batch:
     def step_and_render(self, stream=None):
         self._check(self._lib.mmr_batch_step_and_render(self._h, stream_handle(stream)))
 
+    def step_and_render_roundtrip(self, stream=None, pinned: bool = True):
+        """One frame through a device -> host -> device copy of all positions (see include/mmr.h)."""
+        self._check(self._lib.mmr_batch_step_and_render_roundtrip(self._h, stream_handle(stream), int(pinned)))
+
     def run_graph(self, frames: int, stream=None):
         self._check(self._lib.mmr_batch_run_graph(self._h, frames, stream_handle(stream)))
 

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -69,6 +70,7 @@ struct BatchTables {
     uint32_t *remaining;        // [count] unfinished point items per cloud, reset before every frame
     uint32_t *err;              // bit 0: a bounded wait gave up
     struct ItemParams *params;  // [count] this frame's parameters of each cloud
+    long long pos_shift;        // bytes added to every cloud's position pointer (render from a copy)
 };
 
 // A cloud's parameters for one frame, built once per frame for all clouds
@@ -106,7 +108,7 @@ __global__ void batch_params_kernel(BatchTables T)
     P.disc_r = 0.0f;
     P.disc_r2 = 0.0f;
     philox_prepare(P);
-    I.pos = cl.pos;
+    I.pos = reinterpret_cast<void *>(reinterpret_cast<uintptr_t>(cl.pos) + T.pos_shift);
     I.n = cl.n;
     I.pad = 0;
     T.params[c] = I;
@@ -156,8 +158,10 @@ __device__ __forceinline__ void resolve_quad_l2(const unsigned long long *keys, 
 // it works on a point item, or after a pixel item's wait: an item is never
 // held by a CTA that is waiting.  Measured on the 256-cloud scene against one
 // thread building the parameters per item and the next item taken after the
-// current one: 0.770 -> 0.748 ms per frame.
-template <int DT>
+// current one: 0.770 -> 0.748 ms per frame.  The host round trip runs it twice
+// per frame: displace only (pixel items skipped), then render only from the
+// copied positions.
+template <int DT, bool kDisplace, bool kSplat>
 __global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTables T)
 {
     constexpr uint32_t G = Group<DT>::kPoints;
@@ -174,12 +178,14 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTabl
         uint32_t nxt = 0;
         if (w.x & kPixelItem) {
             if (threadIdx.x == 0) {
-                s_ok = wait_until_zero(T.remaining + cloud, T.spin_limit, T.err);
-                __threadfence();
+                if constexpr (kSplat) {
+                    s_ok = wait_until_zero(T.remaining + cloud, T.spin_limit, T.err);
+                    __threadfence();
+                }
                 nxt = atomicAdd(T.next, 1u);    // taken only after the wait: a held item never waits behind one
             }
             __syncthreads();
-            if (s_ok) {
+            if (kSplat && s_ok) {
                 const CloudDev &cl = T.clouds[cloud];
                 const unsigned long long *keys = cl.keys[buf];
                 unsigned long long *nk = cl.keys[buf ^ 1];
@@ -213,16 +219,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTabl
                 if (g < full) {
                     uint4 q[3];
                     load_words(pos, g, q);
-                    process_words<DT, true, true>(q, g * G, G, sI.P);
-                    store_words(pos, g, q);
+                    process_words<DT, kDisplace, kSplat>(q, g * G, G, sI.P);
+                    if constexpr (kDisplace)
+                        store_words(pos, g, q);
                 } else {
-                    process_tail<DT, true, true>(pos, pos, n, g * G, sI.P);
+                    process_tail<DT, kDisplace, kSplat>(pos, pos, n, g * G, sI.P);
                 }
             }
             if (threadIdx.x == 0)
                 s_next = nxt;
             __syncthreads();                     // every thread's atomics and stores precede the count below
-            if (threadIdx.x == 0) {
+            if (kSplat && threadIdx.x == 0) {
                 __threadfence();
                 atomicSub(T.remaining + cloud, 1u);
             }
@@ -272,6 +279,9 @@ struct mmr_batch {
     uint32_t *d_work = nullptr;      // [0] next item, [1] error bits, [2] self-test count (never zero)
     uint32_t *d_remaining = nullptr; // [count] unfinished point items per cloud, then [count] their full counts
     mmr::ItemParams *d_params = nullptr;
+    void *rt_host = nullptr;         // host round trip: host copy of the positions (pinned or pageable)
+    int rt_host_pinned = -1;
+    void *rt_device = nullptr;       // and the device buffer the copy comes back to
 
     std::vector<mmr::Cam> cams;      // host copy [slots][count]
     std::vector<uint8_t> cam_set;
@@ -350,15 +360,15 @@ cudaError_t resident_grid(const mmr_batch *b, int *grid)
         cudaError_t e;
         switch (b->dtype) {
         case MMR_F32x3:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kF32>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kF32, true, true>,
                                                               b->launch.threads, 0);
             break;
         case MMR_F16x3:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kF16>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kF16, true, true>,
                                                               b->launch.threads, 0);
             break;
         default:
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kBF16>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mmr::batch_frame_kernel<mmr::kBF16, true, true>,
                                                               b->launch.threads, 0);
             break;
         }
@@ -447,6 +457,7 @@ mmr::BatchTables tables(const mmr_batch *b)
     T.remaining = b->d_remaining;
     T.err = b->d_work + 1;
     T.params = b->d_params;
+    T.pos_shift = 0;
     return T;
 }
 
@@ -467,12 +478,26 @@ mmr_status upload_cameras(mmr_batch *b, cudaStream_t s)
     return MMR_OK;
 }
 
-// Enqueue one frame on s: reset the hand-out counter and the per-cloud
-// counts, build every cloud's parameters for the frame, one persistent
-// launch, advance the frame counter.  No host synchronisation.
-cudaError_t enqueue_frame(const mmr_batch *b, cudaStream_t s)
+enum class Pass { kFrame, kDisplace, kRender };
+
+template <int DT>
+cudaError_t launch_pass(const mmr_batch *b, cudaStream_t s, const mmr::BatchTables &T, Pass pass)
 {
-    const mmr::BatchTables T = tables(b);
+    switch (pass) {
+    case Pass::kFrame: mmr::batch_frame_kernel<DT, true, true><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    case Pass::kDisplace: mmr::batch_frame_kernel<DT, true, false><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    default: mmr::batch_frame_kernel<DT, false, true><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    }
+    return cudaGetLastError();
+}
+
+// Enqueue one pass over the work list on s: reset the hand-out counter and
+// the per-cloud counts, build every cloud's parameters for the frame (its
+// positions `shift` bytes from its own buffer), one persistent launch.
+cudaError_t enqueue_pass(const mmr_batch *b, cudaStream_t s, Pass pass, long long shift)
+{
+    mmr::BatchTables T = tables(b);
+    T.pos_shift = shift;
     cudaError_t e = cudaMemsetAsync(b->d_work, 0, sizeof(uint32_t), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_remaining, b->d_remaining + b->count, sizeof(uint32_t) * b->count,
@@ -481,11 +506,17 @@ cudaError_t enqueue_frame(const mmr_batch *b, cudaStream_t s)
         return e;
     mmr::batch_params_kernel<<<(b->count + 127) / 128, 128, 0, s>>>(T);
     switch (b->dtype) {
-    case MMR_F32x3: mmr::batch_frame_kernel<mmr::kF32><<<b->grid, b->launch.threads, 0, s>>>(T); break;
-    case MMR_F16x3: mmr::batch_frame_kernel<mmr::kF16><<<b->grid, b->launch.threads, 0, s>>>(T); break;
-    default: mmr::batch_frame_kernel<mmr::kBF16><<<b->grid, b->launch.threads, 0, s>>>(T); break;
+    case MMR_F32x3: return launch_pass<mmr::kF32>(b, s, T, pass);
+    case MMR_F16x3: return launch_pass<mmr::kF16>(b, s, T, pass);
+    default: return launch_pass<mmr::kBF16>(b, s, T, pass);
     }
-    e = cudaGetLastError();
+}
+
+// Enqueue one frame on s (one pass, then advance the frame counter); no host
+// synchronisation.
+cudaError_t enqueue_frame(const mmr_batch *b, cudaStream_t s)
+{
+    cudaError_t e = enqueue_pass(b, s, Pass::kFrame, 0);
     if (e != cudaSuccess)
         return e;
     mmr::batch_advance_kernel<<<1, 1, 0, s>>>(b->d_frame);
@@ -534,6 +565,13 @@ mmr_status mmr_batch_destroy(mmr_batch *b)
     bfree(b, (void **)&b->d_work, 3 * sizeof(uint32_t));
     bfree(b, (void **)&b->d_remaining, 2 * sizeof(uint32_t) * (uint64_t)b->count);
     bfree(b, (void **)&b->d_params, sizeof(mmr::ItemParams) * (uint64_t)b->count);
+    bfree(b, &b->rt_device, b->pos_bytes);
+    if (b->rt_host) {
+        if (b->rt_host_pinned == 1)
+            cudaFreeHost(b->rt_host);
+        else
+            free(b->rt_host);
+    }
     if (b->staging)
         cudaFreeHost(b->staging);
     if (b->staging_done)
@@ -737,6 +775,68 @@ mmr_status mmr_batch_step_and_render(mmr_batch *b, void *stream)
     cudaError_t e = enqueue_frame(b, s);
     if (e != cudaSuccess)
         return bcuda(b, e, "batch frame launch");
+    b->frames += 1;
+    return MMR_OK;
+}
+
+mmr_status mmr_batch_step_and_render_roundtrip(mmr_batch *b, void *stream, int pinned_host)
+{
+    mmr::NvtxRange nvtx("mmr_batch_step_and_render_roundtrip");
+    if (!b)
+        return MMR_ERR_INVALID_ARG;
+    mmr_status st = cameras_ready(b, false);
+    if (st != MMR_OK)
+        return st;
+    const int want_pinned = pinned_host ? 1 : 0;
+    if (b->rt_host && b->rt_host_pinned != want_pinned) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess)
+            return bcuda(b, e, "batch round trip: sync before switching host buffer");
+        if (b->rt_host_pinned == 1)
+            cudaFreeHost(b->rt_host);
+        else
+            free(b->rt_host);
+        b->rt_host = nullptr;
+    }
+    if (!b->rt_host) {
+        if (want_pinned) {
+            cudaError_t e = cudaMallocHost(&b->rt_host, b->pos_bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                b->rt_host = nullptr;
+                return bfail(b, MMR_ERR_OOM, "batch round trip: pinned host allocation failed: %s",
+                             cudaGetErrorString(e));
+            }
+        } else {
+            b->rt_host = malloc(b->pos_bytes);
+            if (!b->rt_host)
+                return bfail(b, MMR_ERR_OOM, "batch round trip: host allocation failed");
+        }
+        b->rt_host_pinned = want_pinned;
+    }
+    if (!b->rt_device) {
+        st = balloc(b, &b->rt_device, b->pos_bytes, "batch round-trip device copy");
+        if (st != MMR_OK)
+            return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st = upload_cameras(b, s);
+    if (st != MMR_OK)
+        return st;
+    cudaError_t e = enqueue_pass(b, s, Pass::kDisplace, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->rt_host, b->pos_base, b->pos_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->rt_device, b->rt_host, b->pos_bytes, cudaMemcpyHostToDevice, s);
+    const long long shift = (long long)((uintptr_t)b->rt_device - (uintptr_t)b->pos_base);
+    if (e == cudaSuccess)
+        e = enqueue_pass(b, s, Pass::kRender, shift);
+    if (e == cudaSuccess) {
+        mmr::batch_advance_kernel<<<1, 1, 0, s>>>(b->d_frame);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return bcuda(b, e, "batch round-trip frame");
     b->frames += 1;
     return MMR_OK;
 }

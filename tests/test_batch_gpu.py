@@ -86,6 +86,25 @@ def test_batch_direct_matches_oracle_per_cloud(dtype):
         _check_all(b, clouds, stored, eyes, dtype, frames)
 
 
+@pytest.mark.parametrize("dtype,pinned", [("f32", True), ("f16", False), ("bf16", True)])
+def test_batch_roundtrip_matches_oracle_per_cloud(dtype, pinned):
+    """The host round trip (displace, positions device -> host -> device,
+    render from the copy) mixed with zero-copy frames: every cloud still
+    equals its oracle run."""
+    from paper_2504_20937_b300.api import Batch
+    clouds, stored, eyes = _make(RAGGED, dtype, seed=3)
+    frames = 4
+    with Batch(clouds, dtype, camera_slots=frames) as b:
+        _upload(b, stored)
+        _set_cameras(b, eyes, frames)
+        b.step_and_render_roundtrip(pinned=pinned)
+        b.step_and_render()
+        b.step_and_render_roundtrip(pinned=not pinned)       # switching host buffer kinds
+        b.step_and_render_roundtrip(pinned=pinned)
+        assert b.frames == frames
+        _check_all(b, clouds, stored, eyes, dtype, frames)
+
+
 @pytest.mark.parametrize("launch", [(32, 0, 1), (128, 1, 64), (512, 8, 1024), (512, 2, 7), (64, 0, 65536)])
 def test_batch_launch_shapes_and_graph(launch):
     from paper_2504_20937_b300.api import Batch
