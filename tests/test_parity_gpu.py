@@ -135,6 +135,35 @@ def test_split_and_roundtrip_paths_match(mode, dtype):
     _assert_same(gpu_run(*args, mode=mode), oracle_run(*args), f"{mode} {dtype}")
 
 
+def test_storage_drift_against_fp64_reported():
+    """Multi-frame drift of each storage type against the FP64 trajectory that
+    starts from the same stored positions, reported at 1, 10 and 100 steps
+    (2^18 uniform points, a = 5e-4 as in the 2^22-point orbit).  Gated only by
+    the worst case: both sides draw the same offsets and the clamp cannot
+    enlarge a difference, so each step adds at most the storage rounding of a
+    value in [0, 1] (h: half an ulp below 1, 2^-12 binary16, 2^-9 bfloat16, 0
+    FP32) plus the FP32 rounding of p + d and of d (< 2^-23): after T steps
+    |delta| <= T (h + 2^-23)."""
+    n, a, seed = 1 << 18, 5e-4, 12
+    pos0 = inputs.uniform_cloud(n, 41)
+    half_ulp = {"f32": 0.0, "f16": 2.0**-12, "bf16": 2.0**-9}
+    report = {}
+    for dtype in ("f32", "f16", "bf16"):
+        stored = inputs.encode(pos0, dtype)
+        p64 = oracle.from_storage(stored, dtype).astype(np.float64)
+        done, report[dtype] = 0, {}
+        for T in (1, 10, 100):
+            while done < T:
+                oracle.displace_f64(p64, seed, 0, done, float(np.float32(a)))
+                done += 1
+            g = gpu_run(stored, dtype, 64, 64, seed, a, T, fixed_eye)
+            got = oracle.from_storage(g[0], dtype).astype(np.float64)
+            d = np.abs(got - p64)
+            report[dtype][T] = {"max_abs": float(d.max()), "rms_abs": float(np.sqrt(np.mean(d * d)))}
+            assert d.max() <= T * (half_ulp[dtype] + 2.0**-23), (dtype, T, float(d.max()))
+    print("storage drift against the FP64 trajectory:", report)
+
+
 def test_colour_buffer_and_style():
     n = 30_000
     stored = inputs.encode(inputs.uniform_cloud(n, 24), "f32")
