@@ -254,9 +254,9 @@ MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
  * displacement parameters, advanced and rendered together by one persistent
  * launch per frame.  Its CTAs take work items from one list: each cloud's
  * point items (displace, project, splat), and that cloud's pixel items
- * (resolve, clear) placed about one resident grid later, so that its
- * depth-id buffer is normally still in L2 when it is resolved.  A pixel item
- * waits, bounded, until its cloud's point items are done; a wait that gives
+ * (resolve, clear) placed about one resident grid later, so that streaming
+ * pixel work runs beside latency-bound point work.  A pixel item waits,
+ * bounded, until its cloud's point items are done; a wait that gives
  * up raises the batch's device error flag (mmr_batch_check_device).  A
  * device-side frame counter picks the Philox step, the camera slot and the
  * depth-id buffer, so one captured frame can be replayed as a CUDA graph

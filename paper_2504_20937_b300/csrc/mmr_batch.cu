@@ -10,13 +10,15 @@
 // their size and no CTA idles on a small cloud.  The list holds every
 // cloud's point items in order, and a cloud's pixel items once about one
 // resident grid's worth of later point items precede them: by the time they
-// are taken the cloud's points are normally done and its depth-id buffer is
-// still in L2, so the resolve reads it from there rather than from DRAM.  A
-// pixel item waits (bounded) for its cloud's count of unfinished point items
-// to reach zero; every point item it waits on was taken earlier by a running
-// CTA and never waits itself, so the wait ends.  A device-side frame counter
-// selects the Philox step, the camera slot and the depth-id buffer, so a
-// captured frame replays as a CUDA graph with no host update.
+// are taken the cloud's points are normally done, and the bandwidth-bound
+// resolve runs beside other clouds' latency-bound point items (on the
+// 256-cloud scene the keys still come back from DRAM; the gain is that
+// overlap).  A pixel item waits (bounded) for its cloud's count of
+// unfinished point items to reach zero; every point item it waits on was
+// taken earlier by a running CTA and never waits itself, so the wait ends.
+// A device-side frame counter selects the Philox step, the camera slot and
+// the depth-id buffer, so a captured frame replays as a CUDA graph with no
+// host update.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
