@@ -36,6 +36,7 @@
 #include "mmr_internal.h"
 #include "mmr_points.cuh"
 #include "mmr_resolve.cuh"
+#include "mmr_worklist.h"
 
 namespace mmr {
 
@@ -52,9 +53,6 @@ struct CloudDev {
     uint32_t color, background;
 };
 
-// Item word x: the cloud, with this bit set for a pixel item; y: the first
-// point group (point item) or quad (pixel item).
-constexpr uint32_t kPixelItem = 0x80000000u;
 
 struct BatchTables {
     const CloudDev *clouds;
@@ -393,35 +391,16 @@ mmr_status build_items(mmr_batch *b)
     cudaError_t e = resident_grid(b, &grid);
     if (e != cudaSuccess)
         return bcuda(b, e, "occupancy query");
-    const uint32_t cq = chunk_quads(b);
-    std::vector<uint2> items;
-    std::vector<uint32_t> counts(2 * (size_t)b->count, 0);
-    std::vector<std::pair<uint32_t, uint64_t>> done;     // (cloud, point items listed after its last one)
-    uint64_t listed = 0;
-    size_t head = 0;
-    auto push_pixels = [&](uint32_t c) {
-        const uint32_t quads = (uint32_t)(((uint64_t)b->desc[c].width * b->desc[c].height) / 4);
-        uint32_t q = 0;
-        do {                          // at least one item per cloud: it owns the ragged tail
-            items.push_back(make_uint2(c | mmr::kPixelItem, q));
-            q += cq;
-        } while (q < quads);
-    };
+    std::vector<uint32_t> groups(b->count), quads(b->count), per_cloud;
     for (int c = 0; c < b->count; ++c) {
-        const uint32_t groups = groups_for(b->desc[c].n, b->dtype);
-        for (uint32_t g = 0; g < groups; g += b->chunk_groups) {
-            items.push_back(make_uint2((uint32_t)c, g));
-            counts[c] += 1;
-            ++listed;
-            while (head < done.size() && listed - done[head].second >= (uint64_t)grid)
-                push_pixels(done[head++].first);
-        }
-        done.push_back({(uint32_t)c, listed});
+        groups[c] = groups_for(b->desc[c].n, b->dtype);
+        quads[c] = (uint32_t)(((uint64_t)b->desc[c].width * b->desc[c].height) / 4);
     }
-    while (head < done.size())
-        push_pixels(done[head++].first);
-    for (int c = 0; c < b->count; ++c)
-        counts[b->count + c] = counts[c];
+    static_assert(sizeof(mmr::WorkItem) == sizeof(uint2), "a work item is uploaded as a uint2");
+    const std::vector<mmr::WorkItem> items =
+        mmr::build_work_list(groups, quads, b->chunk_groups, chunk_quads(b), (uint64_t)grid, per_cloud);
+    std::vector<uint32_t> counts(per_cloud);                 // [count] live counts, then [count] full counts
+    counts.insert(counts.end(), per_cloud.begin(), per_cloud.end());
     bfree(b, (void **)&b->d_items, b->item_bytes);
     b->n_items = 0;                  // until the new list is in place a frame hands out nothing
     b->item_bytes = items.size() * sizeof(uint2);
