@@ -163,26 +163,35 @@ class Clocks:
         if not self.file:
             return None
         try:
-            rows = [r.split(",") for r in open(self.file.name).read().strip().splitlines() if r.strip()]
+            text = open(self.file.name).read()
             os.unlink(self.file.name)
         except Exception:
             return None
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[0]))
-                mx.append(float(r[1]))
-                for name, v in zip(names, r[3:7]):
-                    if "Active" in v and "Not" not in v:
-                        reasons.add(name)
-            except (ValueError, IndexError):
-                continue
-        if not sm:
-            return None
-        busy = [s for s in sm if s > 0.5 * max(sm)]
-        return {"sm_mhz": statistics.median(busy or sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return summarize_clock_samples(text)
+
+
+def summarize_clock_samples(text: str):
+    """Median SM clock under load (samples above half the highest), the
+    maximum SM clock and the throttle reasons seen Active, from nvidia-smi
+    rows of Clocks.FIELDS (csv, no header, no units); None without a sample."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in text.strip().splitlines():
+        r = [v.strip() for v in line.split(",")]
+        try:
+            s, m = float(r[0]), float(r[1])
+        except (ValueError, IndexError):
+            continue
+        sm.append(s)
+        mx.append(m)
+        for name, v in zip(names, r[3:7]):
+            if v == "Active":
+                reasons.add(name)
+    if not sm:
+        return None
+    busy = [s for s in sm if s > 0.5 * max(sm)]
+    return {"sm_mhz": statistics.median(busy or sm), "sm_max_mhz": max(mx), "samples": len(sm),
+            "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------- multi-rank glue

@@ -45,3 +45,21 @@ def test_single_process_reduce_is_identity():
     import bench
     assert bench.reduce_max(3.5) == 3.5
     assert bench.job_rate(10.0, 1, 1000.0) == 10.0
+
+
+def test_clock_sample_summary():
+    """The clocks record beside a bench number: median SM clock under load,
+    maximum clock, and only the throttle reasons reported Active."""
+    import bench
+    rows = "\n".join([
+        "345, 2032, 120.5, Not Active, Not Active, Not Active, Not Active",      # idle before the region
+        "2032, 2032, 900.1, Not Active, Not Active, Not Active, Not Active",
+        "2017, 2032, 1099.0, Not Active, Not Active, Not Active, Active",         # power cap: kept, noted
+        "2032, 2032, 950.0, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], 2032, 10.0, Not Active, Not Active, Not Active, Not Active",      # unreadable sample skipped
+    ])
+    s = bench.summarize_clock_samples(rows)
+    assert s == {"sm_mhz": 2032.0, "sm_max_mhz": 2032.0, "samples": 4, "reasons": ["sw_power_cap"]}
+    hot = bench.summarize_clock_samples("1500, 2032, 1000, Active, Not Active, Active, Not Active")
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.summarize_clock_samples("") is None
