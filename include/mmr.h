@@ -23,7 +23,8 @@
  *    independent.
  *  - Errors return a negative mmr_status; nothing aborts the process and no
  *    kernel traps.  mmr_last_error(ctx) gives a message for the last failure
- *    on that context.
+ *    on that context.  The status codes and messages are this library's own
+ *    convention: the paper specifies no error reporting.
  */
 #ifndef MMR_H
 #define MMR_H
@@ -44,6 +45,7 @@ extern "C" {
 typedef struct mmr_ctx mmr_ctx;
 typedef int mmr_status;
 
+/* Status codes: this library's chosen convention (the paper defines none). */
 enum {
     MMR_OK = 0,
     MMR_ERR_INVALID_ARG = -1,  /* a pointer is NULL, a size is 0 or too large, a value out of range */
@@ -72,12 +74,16 @@ MMR_API mmr_status mmr_create(int width, int height, mmr_ctx **out);
 MMR_API mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx **out);
 
 /* Release every device and host allocation of the context (the points
- * pointer included).  Waits for work the context enqueued to finish.  A NULL
- * ctx is a no-op.  Every pointer the context handed out is invalid after. */
+ * pointer included), as destroying a Mimir handle cleans up the resources
+ * created with it (Sec. 3.2.2).  Waits for work the context enqueued to
+ * finish.  A NULL ctx is a no-op.  Every pointer the context handed out is
+ * invalid after. */
 MMR_API mmr_status mmr_destroy(mmr_ctx *ctx);
 
 /* Message of the last failure on ctx ("" if none); for a NULL ctx, the last
- * failure of mmr_create in this process.  Valid until the next call on ctx. */
+ * failure of mmr_create or mmr_render_static in this process.  Valid until
+ * the next call on ctx.  Like the status codes, a convention of this library
+ * (the paper specifies no error reporting). */
 MMR_API const char *mmr_last_error(const mmr_ctx *ctx);
 MMR_API const char *mmr_status_string(mmr_status s);
 
@@ -173,11 +179,15 @@ MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, in
 
 /* ---- frames ---------------------------------------------------------------- */
 
-/* One frame: displace every point (current step), project and depth-splat
- * it (key = bits(clip w) << 32 | point id, per-pixel minimum), then resolve
- * the keys to RGBA8.  Displacement and splat are one fused kernel; resolve
- * also clears the other depth-id buffer for the next frame.  Advances the
- * step counter.  Requires points and a camera. */
+/* One frame of the paper's benchmark (Sec. 4.1): a compute step moves every
+ * point by Brownian motion and the new state is drawn, the compute section
+ * and the render that follows it being what display / prepareViews +
+ * updateViews order (Sec. 3.4, Listing 2).  Here: displace every point
+ * (current step), project and depth-splat it (key = bits(clip w) << 32 |
+ * point id, per-pixel minimum), then resolve the keys to RGBA8, all enqueued
+ * on `stream` in that order.  Displacement and splat are one fused kernel;
+ * resolve also clears the other depth-id buffer for the next frame.
+ * Advances the step counter.  Requires points and a camera. */
 MMR_API mmr_status mmr_step_and_render(mmr_ctx *ctx, void *stream);
 
 /* One frame out of place (ping-pong): read the visible buffer, write the
@@ -218,9 +228,12 @@ MMR_API mmr_status mmr_render(mmr_ctx *ctx, void *stream);
 MMR_API mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int pinned_host);
 
 /* Device pointers of the latest frame: RGBA8 (width*height uint32) and its
- * depth-id keys (width*height uint64, all-ones = empty).  Valid after the
- * stream that rendered the frame is synchronised, until the next frame or
- * mmr_destroy.  Either output pointer may be NULL. */
+ * depth-id keys (width*height uint64, all-ones = empty).  This is the device
+ * memory a display would read, as the paper's renderer reads the latest state
+ * straight from memory shared with the compute side instead of a host copy
+ * (Sec. 1, Sec. 3.2.1).  Valid after the stream that rendered the frame is
+ * synchronised, until the next frame or mmr_destroy.  Either output pointer
+ * may be NULL. */
 MMR_API mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **depth_id);
 
 /* Current step counter (index of the next displacement step). */
@@ -444,8 +457,13 @@ MMR_API mmr_status mmr_serve_last_tick_ms(mmr_serve *s, float *ms);
  * fixed-size array inside the library.
  *
  * MMR_STATIC_MAX_PIXELS: capacity of that array, in pixels (8 bytes each,
- * 32 MiB).  Every GPU on which the library is loaded holds the array until
- * the process exits, whether or not this function is called.
+ * 32 MiB).  The array is device memory of its own code module, which CUDA
+ * loads on a device when it is first used there (lazy module loading, the
+ * default): the first call of this function on a device reserves the
+ * 32 MiB, and the device keeps them until the process exits.  A caller whose
+ * memory manager claims the rest of the device should make that first call
+ * at start-up, before the claim; if the array cannot be loaded the call
+ * fails with MMR_ERR_OOM (or MMR_ERR_CUDA) and the CUDA error text.
  *
  * mmr_render_static: render n points (dtype as mmr_alloc_points; dev_points
  * 16-byte aligned, n*3 coordinates, AoS, read only) with the FP32 row-major
@@ -455,11 +473,14 @@ MMR_API mmr_status mmr_serve_last_tick_ms(mmr_serve *s, float *ms);
  * what mmr_set_matrix + mmr_render produce for the same points.
  *  - Allocates nothing: no cudaMalloc, cudaFree or other allocating call.
  *  - width*height above MMR_STATIC_MAX_PIXELS, n outside 1..2^32-1, a NULL
- *    pointer, a misaligned dev_points or a depth range outside
- *    2^-64 <= znear < zfar <= 2^64: MMR_ERR_INVALID_ARG, nothing launched.
+ *    pointer, dev_points not 16-byte aligned, dev_rgba not 4-byte aligned
+ *    or a depth range outside 2^-64 <= znear < zfar <= 2^64:
+ *    MMR_ERR_INVALID_ARG, nothing launched.
  *  - The first call on a device (with that device current) looks up the
- *    array's device address once; make that first call before any CUDA
- *    stream capture that contains this call.
+ *    array's device address once and keeps it; make that first call before
+ *    any CUDA stream capture that contains this call.  The kept address
+ *    assumes the device is not reset (cudaDeviceReset) while the library is
+ *    in use.
  *  - Every call on a device shares the one array.  Each call clears the
  *    part it uses before drawing, but calls whose work overlaps on the GPU
  *    (different streams, or threads without ordering between them) race on

@@ -555,9 +555,6 @@ mmr_status mmr_alloc_indexed_colors(mmr_ctx *ctx, uint32_t ncolors, uint32_t **d
         st = dev_alloc(ctx, (void **)&ctx->colormap, (uint64_t)ncolors * 4, "colormap");
     if (st != MMR_OK) {
         dev_free(ctx, (void **)&ctx->index, ctx->n * 4);
-    dev_free(ctx, (void **)&ctx->nb_vel, ctx->n * 12);
-    dev_free(ctx, (void **)&ctx->nb_mass, ctx->n * 4);
-    dev_free(ctx, (void **)&ctx->nb_partial, (uint64_t)mmr::nbody_chunks((uint32_t)ctx->n) * ctx->n * 16);
         return st;
     }
     ctx->ncolors = ncolors;

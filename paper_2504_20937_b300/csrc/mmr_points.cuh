@@ -193,10 +193,12 @@ __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32
     }
 }
 
+// Groups covering n points, the last one possibly partial.  The sum is taken
+// in 64 bits: n may be as large as 2^32 - 1, where n + G - 1 would wrap.
 template <int DT>
 __host__ __device__ constexpr uint32_t groups_of(uint32_t n)
 {
-    return (n + Group<DT>::kPoints - 1) / Group<DT>::kPoints;
+    return (uint32_t)(((uint64_t)n + Group<DT>::kPoints - 1) / Group<DT>::kPoints);
 }
 
 }  // namespace mmr

@@ -1,13 +1,20 @@
 // mmr_render_static: render without allocating device memory.
 //
-// The depth-id scratch of this entry point is a file-scope __device__ array,
-// created when the library's module is loaded on a device and kept until the
-// process exits.  Host code cannot use the array's name as a device address
-// (on the host it names a stand-in object), so the address is looked up once
-// per device with cudaGetSymbolAddress while that device is current, cached,
-// and passed to the kernels as a plain pointer.
+// The depth-id scratch of this entry point is a file-scope __device__ array.
+// This file is its own device module (the library is linked without
+// relocatable device code), and under CUDA's lazy module loading, the default,
+// a module is loaded on a device when it is first used there: the array's
+// 32 MiB are reserved by the first call on each device (its
+// cudaGetSymbolAddress), not when the library is loaded, and stay reserved
+// until the process exits.  Host code cannot use the array's name as a device
+// address (on the host it names a stand-in object), so the address is looked
+// up once per device with cudaGetSymbolAddress while that device is current,
+// cached, and passed to the kernels as a plain pointer.  The cache assumes the
+// device's primary context lives as long as the process: after a
+// cudaDeviceReset the cached address is stale.
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -91,11 +98,17 @@ extern "C" mmr_status mmr_render_static(const void *dev_points, uint64_t n, int 
         return static_fail(MMR_ERR_INVALID_ARG, "mmr_render_static: need 2^-64 <= znear < zfar <= 2^64");
     if (reinterpret_cast<uintptr_t>(dev_points) % 16 != 0)
         return static_fail(MMR_ERR_INVALID_ARG, "mmr_render_static: dev_points must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(dev_rgba) % 4 != 0)
+        return static_fail(MMR_ERR_INVALID_ARG, "mmr_render_static: dev_rgba must be 4-byte aligned");
     unsigned long long *keys = nullptr;
     cudaError_t e = static_keys_on_current_device(&keys);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return static_fail(MMR_ERR_CUDA, "mmr_render_static: cudaGetSymbolAddress of the scratch array failed");
+        char msg[256];
+        snprintf(msg, sizeof msg,
+                 "mmr_render_static: loading the 32 MiB scratch array on this device (cudaGetSymbolAddress) "
+                 "failed: %s", cudaGetErrorString(e));
+        return static_fail(e == cudaErrorMemoryAllocation ? MMR_ERR_OOM : MMR_ERR_CUDA, msg);
     }
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -132,7 +145,10 @@ extern "C" mmr_status mmr_render_static(const void *dev_points, uint64_t n, int 
         static_resolve_kernel<<<grid_px, 256, 0, s>>>(keys, dev_rgba, npx, color, background);
         e = cudaGetLastError();
     }
-    if (e != cudaSuccess)
-        return static_fail(MMR_ERR_CUDA, "mmr_render_static: kernel launch failed");
+    if (e != cudaSuccess) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "mmr_render_static: kernel launch failed: %s", cudaGetErrorString(e));
+        return static_fail(MMR_ERR_CUDA, msg);
+    }
     return MMR_OK;
 }

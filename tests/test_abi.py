@@ -73,3 +73,18 @@ def test_create_without_gpu_reports_cuda_error():
     st = lib.mmr_create(64, 64, C.byref(h))
     assert st == -4 and h.value is None
     assert b"CUDA" in lib.mmr_last_error(None) or b"cuda" in lib.mmr_last_error(None)
+
+
+def test_group_counts_at_the_largest_point_counts():
+    """groups_of (csrc/mmr_points.cuh) for n up to 2^32 - 1, checked by
+    static_asserts that nvcc evaluates on the host (no GPU needed)."""
+    out_dir = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    obj = os.path.join(out_dir, f"groups_check_{os.getpid()}.o")
+    r = subprocess.run(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17",
+                        "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "paper_2504_20937_b300", "csrc"),
+                        "-c", os.path.join(ROOT, "tests", "cuda", "groups_check.cu"), "-o", obj],
+                       capture_output=True, text=True)
+    if os.path.exists(obj):
+        os.remove(obj)
+    assert r.returncode == 0, r.stderr
