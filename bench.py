@@ -7,13 +7,16 @@ depth-id buffer, then a resolve kernel writes the RGBA8 framebuffer and
 clears the next depth-id buffer.  Inputs are resident in device memory when
 the timed region starts.
 
-Default workload: 2^22 FP32 points uniform in [0,1]^3, 1920x1080, camera
-orbiting the centre at 0.36 deg/frame, a = 5e-4.  L2 is flushed (a 512 MB
-read, leaving only clean lines) before every timed frame; each frame is timed with CUDA events on the
-launching stream.  Also reported on the same run: the host round-trip path
-(positions device -> host -> device every frame), the end-to-end rate
-through the public API with each frame read back to host memory, and the
-64M-point 16-cluster 3840x2160 frame in FP32 / binary16 / bfloat16 storage.
+Default workload (the headline): 2^26 = 67,108,864 FP32 points drawn from a
+16-component isotropic Gaussian mixture (sigma 0.02), 3840x2160, fixed
+camera, a = 5e-4.  Its 805 MB of positions are larger than L2 (126 MB), so
+no flush is needed between frames; each frame is timed with CUDA events on
+the launching stream.  Also reported on the same run: the host round-trip
+path (positions device -> host -> device every frame), the end-to-end rate
+through the public API with each frame read back to host memory, the error
+of each storage type against the FP64 oracle, the same frame in binary16 and
+bfloat16 storage, the 2^22-point 1920x1080 orbit (L2 flushed before every
+frame), and the batched and served forms.
 
 `--impl reference` times the CPU oracle (single-threaded C) on the same
 workload instead.  Prints ONE JSON line on rank 0.
@@ -39,6 +42,7 @@ from paper_2504_20937_b300 import inputs  # noqa: E402
 
 METRIC = "points/s (displace+render)"
 FLUSH_BYTES = 512 << 20
+L2_BYTES = 126 << 20
 CENTRE = (0.5, 0.5, 0.5)
 UP = (0.0, 1.0, 0.0)
 
@@ -53,9 +57,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "pr1", "c3"])
-    ap.add_argument("--no-extra", action="store_true", help="skip the 64M-point and round-trip legs")
-    ap.add_argument("--cpu-frames", type=int, default=60, help="oracle frames for the CPU baseline (0: skip)")
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "pr1"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the legs beside the main timed region")
+    ap.add_argument("--cpu-frames", type=int, default=-1,
+                    help="oracle frames for the CPU baseline (0: skip; -1: 6 on the 64M-point workload, else 60)")
     ap.add_argument("--cpu-omp-seconds", type=float, default=8.0,
                     help="seconds of OpenMP CPU-baseline frames on all host cores (0: skip)")
     ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
@@ -217,6 +222,13 @@ def job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
 
 # --------------------------------------------------------------------- ours
 
+def needs_flush(sc, storage) -> bool:
+    """L2 is flushed before every timed frame unless the positions alone are
+    larger than L2 (126 MB), in which case a frame cannot find the previous
+    frame's positions there anyway."""
+    return sc.n * inputs.BYTES_PER_POINT[storage] < L2_BYTES
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2504_20937_b300.api import Context
@@ -224,7 +236,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc = scene_for(args.workload, args.points)
-    stored = inputs.encode(sc.positions(), "f32")
+    pos64 = sc.positions()
+    stored = inputs.encode(pos64, "f32")
     flush = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     flush_sink = torch.zeros((), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -243,8 +256,8 @@ def run_ours(args, rank, world, local):
     def timed_frames(ctx, scene, frames, warm, do_flush, roundtrip=None, kernel_times=False):
         """Per-frame device times (ms) of the whole step and, with
         kernel_times (the library's per-kernel events switched on), of the
-        point and resolve kernels.  The events between the kernels cost
-        about 5 us per frame, so whole-step times are taken with them off."""
+        point and resolve phases.  The events between the phases cost about
+        5 us per frame, so whole-step times are taken with them off."""
         ctx.set_timing(kernel_times)
         step_ms, point_ms, resolve_ms = [], [], []
         for f in range(warm + frames):
@@ -267,8 +280,10 @@ def run_ours(args, rank, world, local):
                 resolve_ms.append(rk)
         return step_ms, point_ms, resolve_ms
 
+    storage = args.storage
+    do_flush = needs_flush(sc, storage)
     free_before = torch.cuda.mem_get_info(local)[0]
-    ctx = make_ctx(args.storage, stored if args.storage == "f32" else inputs.encode(sc.positions(), args.storage))
+    ctx = make_ctx(storage, stored if storage == "f32" else inputs.encode(pos64, storage))
     zero_copy_bytes = ctx.device_bytes
     zero_copy_measured = free_before - torch.cuda.mem_get_info(local)[0]   # cudaMemGetInfo delta
     if world > 1:
@@ -276,57 +291,62 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         t0 = time.perf_counter()
-        step_ms, _, _ = timed_frames(ctx, sc, args.steps, args.warmup, True)
+        step_ms, _, _ = timed_frames(ctx, sc, args.steps, args.warmup, do_flush)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         # four more repeats of the same K frames: the spread between repeats (`value` is the first)
         repeat_ms = [sum(step_ms) / args.steps]
         for _ in range(4):
-            r_ms, _, _ = timed_frames(ctx, sc, args.steps, 0, True)
+            r_ms, _, _ = timed_frames(ctx, sc, args.steps, 0, do_flush)
             repeat_ms.append(sum(r_ms) / args.steps)
         # the per-kernel durations: a second pass of the same frames with the library's events between the
         # kernels, still under the clock sampler (stopping it perturbs the next few hundred milliseconds)
         kernel_frames = min(args.steps, 200)
-        _, point_ms, resolve_ms = timed_frames(ctx, sc, kernel_frames, 3, True, kernel_times=True)
+        _, point_ms, resolve_ms = timed_frames(ctx, sc, kernel_frames, 3, do_flush, kernel_times=True)
     total_ms = reduce_max(sum(step_ms))
     if world > 1:
         torch.distributed.barrier()
     n = sc.n
     pts_per_s = job_rate(args.steps * n, world, total_ms)
     hbm_gbs, peak_kind = measured_peaks()
-    bytes_point = 2 * inputs.BYTES_PER_POINT[args.storage] * n
+    bytes_point = 2 * inputs.BYTES_PER_POINT[storage] * n
     bytes_frame = bytes_point + 20 * sc.W * sc.H
     mean_point_ms = statistics.mean(point_ms)
     achieved = bytes_point / (mean_point_ms / 1e3) / 1e9
-    traffic = profiled_traffic("points_kernel_f32_fused", sc.name) if args.storage == "f32" else None
-    kernel = "points_kernel<f32, displace, splat>" if args.storage == "f32" else \
-        f"points_kernel_narrow<{args.storage}, displace, splat>"
+    kernel_name = "points_kernel_f32_fused" if storage == "f32" else f"points_kernel_narrow_{storage}_fused"
+    traffic = profiled_traffic(kernel_name, sc.name)
+    kernel = "points_kernel<f32, displace, splat>" if storage == "f32" else \
+        f"points_kernel_narrow<{storage}, displace, splat>"
+    l2_note = (f"flushed before every timed frame ({FLUSH_BYTES >> 20} MB read)" if do_flush else
+               f"not flushed: the {n * inputs.BYTES_PER_POINT[storage] / 1e6:.0f} MB of positions are larger "
+               f"than L2 ({L2_BYTES >> 20} MB)")
 
     out = {
         "metric": METRIC, "value": pts_per_s, "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
-        "data": "synthetic (seeded uniform cloud, numpy PCG64)",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": storage,
+        "data": f"synthetic ({'16-cluster Gaussian mixture' if sc.cloud == 'gmm16' else 'uniform'} cloud, "
+                "numpy PCG64)",
         "config": {"workload": sc.name, "points": n, "width": sc.W, "height": sc.H,
-                   "storage": args.storage, "amplitude": sc.amplitude, "orbit_deg_per_frame": sc.deg_per_frame,
-                   "l2": f"flushed before every timed frame ({FLUSH_BYTES >> 20} MB read)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "launch": args.launch or "library default (grid-stride, 64 threads, one thread per 48-byte group)"},
-        "frames_per_s": job_rate(args.steps, world, total_ms),
-        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-        "repeats": {"ms_per_step": repeat_ms, "median_ms_per_step": float(np.median(repeat_ms)),
-                    "note": "the timed region and four more runs of the same K frames, each L2-flushed frame "
-                            "timed the same way; value is the first"},
-        "hbm_gbs_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9,
-        "kernels_ms": {"points_fused": mean_point_ms, "resolve": statistics.mean(resolve_ms),
-                       "frames": kernel_frames,
-                       "note": "CUDA events around each kernel, in a second pass after the timed region: events "
-                               "between the kernels add about 5 us per frame, so the timed region runs without them"},
+                   "storage": storage, "amplitude": sc.amplitude, "orbit_deg_per_frame": sc.deg_per_frame,
+                   "l2": l2_note, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "launch": args.launch or "library default"},
         "roofline": {"bound": "hbm", "kernel": kernel,
                      "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
                      "traffic": traffic, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": bytes_point},
         "gpu_launches": 2 * args.steps,
+        "frames_per_s": job_rate(args.steps, world, total_ms),
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "hbm_gbs_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9,
+        "frac_step": bytes_frame / (total_ms / args.steps / 1e3) / 1e9 / hbm_gbs,
+        "kernels_ms": {"points_fused": mean_point_ms, "resolve": statistics.mean(resolve_ms),
+                       "frames": kernel_frames,
+                       "note": "CUDA events around each kernel, in a second pass after the timed region: events "
+                               "between the kernels add about 5 us per frame, so the timed region runs without them"},
+        "repeats": {"ms_per_step": repeat_ms, "median_ms_per_step": float(np.median(repeat_ms)),
+                    "note": "the timed region and four more runs of the same K frames, timed the same way; "
+                            "value is the first"},
         "wall_s_timed_region": wall,
         "device_bytes": {"zero_copy": zero_copy_bytes, "zero_copy_cudaMemGetInfo": zero_copy_measured},
     }
@@ -335,22 +355,8 @@ def run_ours(args, rank, world, local):
         out["clocks"] = clocks
 
     if rank == 0 and not args.no_extra:
-        # host round trip (pinned), same frames: the paper's RAM-based comparison
-        rt_frames = min(args.steps, 200)
-        rt_ms, _, _ = timed_frames(ctx, sc, rt_frames, 3, True, roundtrip=True)
-        out["device_bytes"]["roundtrip"] = ctx.device_bytes
-        out["device_bytes"]["roundtrip_cudaMemGetInfo"] = free_before - torch.cuda.mem_get_info(local)[0]
-        out["roundtrip_pinned"] = {"points_per_s": rt_frames * n / (sum(rt_ms) / 1e3),
-                                   "frames_per_s": rt_frames / (sum(rt_ms) / 1e3),
-                                   "p50_ms": float(np.percentile(rt_ms, 50)),
-                                   "p99_ms": float(np.percentile(rt_ms, 99)), "frames": rt_frames,
-                                   "host_bytes_per_frame": 2 * 12 * n}
-        pg_ms, _, _ = timed_frames(ctx, sc, 20, 2, True, roundtrip=False)
-        out["roundtrip_pageable"] = {"points_per_s": 20 * n / (sum(pg_ms) / 1e3),
-                                     "p99_ms": float(np.percentile(pg_ms, 99)), "frames": 20}
-        out["zero_copy_vs_roundtrip_pinned"] = out["value"] / world / out["roundtrip_pinned"]["points_per_s"]
         # end to end through the public API: camera in, every frame read back to pinned host memory
-        e2e_frames = min(args.steps, 300)
+        e2e_frames = min(args.steps, 300 if sc.W * sc.H <= 1 << 22 else 100)
         serial_s = e2e_readback(ctx, sc, e2e_frames, stream, pipelined=False)
         e2e_s = e2e_readback(ctx, sc, e2e_frames, stream, pipelined=True)
         out["e2e"] = {"value": e2e_frames * n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 64,
@@ -361,15 +367,61 @@ def run_ours(args, rank, world, local):
                               "buffer); all copies complete inside the timed region"}
         out["e2e_serial"] = {"value": e2e_frames * n / serial_s, "unit": "points/s", "frames": e2e_frames,
                              "note": "the same, synchronised after every frame's copy (no overlap)"}
+        # host round trip (pinned), same frames: the paper's RAM-based comparison
+        rt_frames = min(args.steps, 200 if n <= 1 << 22 else 20)
+        rt_ms, _, _ = timed_frames(ctx, sc, rt_frames, 3, do_flush, roundtrip=True)
+        out["device_bytes"]["roundtrip"] = ctx.device_bytes
+        out["device_bytes"]["roundtrip_cudaMemGetInfo"] = free_before - torch.cuda.mem_get_info(local)[0]
+        out["roundtrip_pinned"] = {"points_per_s": rt_frames * n / (sum(rt_ms) / 1e3),
+                                   "frames_per_s": rt_frames / (sum(rt_ms) / 1e3),
+                                   "p50_ms": float(np.percentile(rt_ms, 50)),
+                                   "p99_ms": float(np.percentile(rt_ms, 99)), "frames": rt_frames,
+                                   "host_bytes_per_frame": 2 * inputs.BYTES_PER_POINT[storage] * n}
+        pg_frames = 20 if n <= 1 << 22 else 5
+        pg_ms, _, _ = timed_frames(ctx, sc, pg_frames, 2, do_flush, roundtrip=False)
+        out["roundtrip_pageable"] = {"points_per_s": pg_frames * n / (sum(pg_ms) / 1e3),
+                                     "p99_ms": float(np.percentile(pg_ms, 99)), "frames": pg_frames}
+        out["zero_copy_vs_roundtrip_pinned"] = out["value"] / world / out["roundtrip_pinned"]["points_per_s"]
         ctx.close()
-        out["c3_64Mpts_gmm16_3840x2160"] = run_c3(make_ctx, timed_frames, hbm_gbs)
-        out["features_c2"] = run_features(sc, stored, hbm_gbs)
+        # error of one step against the FP64 oracle, for this storage type and the others
+        fp64 = {storage: storage_accuracy(make_ctx, sc, pos64, storage)}
+        others = [d for d in ("f32", "f16", "bf16") if d != storage]
+        legs = run_storage_legs(make_ctx, timed_frames, hbm_gbs, sc, pos64, others, do_flush)
+        for d in others:
+            fp64[d] = storage_accuracy(make_ctx, sc, pos64, d)
+        out["fp64_error"] = fp64
+        out[f"{sc.name}_other_storage"] = legs
+        if sc is not inputs.C2 and not args.points:
+            out[inputs.C2.name] = run_c2_leg(make_ctx, timed_frames, hbm_gbs)
+        out["features_c2"] = run_features(inputs.C2, inputs.encode(inputs.C2.positions(), "f32"), hbm_gbs)
         out["nbody"] = run_nbody()
         out["batched_256_clouds"] = run_batched(hbm_gbs)
         out["served"] = run_served(args.serve_requests)
     else:
         ctx.close()
     return out
+
+
+def storage_accuracy(make_ctx, sc, pos64, dtype):
+    """One step of the workload in `dtype` storage on the GPU, against the
+    same step taken by the FP64 oracle from the same stored input
+    (oracle/accuracy.py, on the host, outside every timed region)."""
+    from oracle import accuracy
+    stored = inputs.encode(pos64, dtype)
+    ctx = make_ctx(dtype, stored, sc)
+    ctx.set_camera(sc.eye(0), CENTRE, UP, sc.fovy_deg, sc.znear, sc.zfar)
+    ctx.step_and_render()
+    got = ctx.points.cpu().numpy()
+    rgba = ctx.frame_rgba().cpu().numpy().reshape(-1).view(np.uint32)
+    ctx.close()
+    got = got if dtype == "f32" else got.view(np.uint16)
+    rep = accuracy.step_accuracy(stored, dtype, got, rgba, sc.philox_seed, 0, 0, sc.amplitude, sc.eye(0), CENTRE,
+                                 UP, sc.fovy_deg, sc.W, sc.H, sc.znear, sc.zfar, sc.color, sc.background)
+    rep["note"] = ("one step from the stored input: relative error |x - x64| / max(|x64|, 2^-14); RGBA agreement "
+                   "with the oracle's frame of the FP64 positions, over all pixels and over pixels covered in "
+                   "either; at-risk pixels: those the stated rounding bound lets change (None when it reaches "
+                   "a pixel)")
+    return rep
 
 
 def e2e_readback(ctx, sc, frames, stream, pipelined):
@@ -429,17 +481,15 @@ def e2e_readback(ctx, sc, frames, stream, pipelined):
     return dt
 
 
-def run_c3(make_ctx, timed_frames, hbm_gbs, frames=20):
-    """64M-point 16-cluster Gaussian mixture at 3840x2160 (inputs larger than
-    L2, no flush needed): FP32, binary16 and bfloat16 storage."""
-    sc = inputs.C3
-    pos64 = sc.positions()
+def run_storage_legs(make_ctx, timed_frames, hbm_gbs, sc, pos64, dtypes, do_flush, frames=20):
+    """The same workload in the other storage types (FP32 compute): frame
+    times with and without the per-kernel events."""
     res = {}
-    for dtype in ("f32", "f16", "bf16"):
+    for dtype in dtypes:
         data = inputs.encode(pos64, dtype)
         ctx = make_ctx(dtype, data, sc)
-        step_ms, _, _ = timed_frames(ctx, sc, frames, 3, False)
-        _, point_ms, resolve_ms = timed_frames(ctx, sc, frames, 1, False, kernel_times=True)
+        step_ms, _, _ = timed_frames(ctx, sc, frames, 3, do_flush)
+        _, point_ms, resolve_ms = timed_frames(ctx, sc, frames, 1, do_flush, kernel_times=True)
         ctx.close()
         bpp = inputs.BYTES_PER_POINT[dtype] * 2
         frame_bytes = bpp * sc.n + 20 * sc.W * sc.H
@@ -448,13 +498,31 @@ def run_c3(make_ctx, timed_frames, hbm_gbs, frames=20):
         res[dtype] = {"ms_per_frame": mean_step, "frames_per_s": 1e3 / mean_step,
                       "points_per_s": sc.n / (mean_step / 1e3),
                       "p99_ms": float(np.percentile(step_ms, 99)),
-                      "hbm_gbs_frame": frame_bytes / (mean_step / 1e3) / 1e9,
                       "frac_frame": frame_bytes / (mean_step / 1e3) / 1e9 / hbm_gbs,
                       "points_kernel_ms": pk, "resolve_ms": statistics.mean(resolve_ms),
-                      "points_kernel_gbs": bpp * sc.n / (pk / 1e3) / 1e9,
                       "points_kernel_frac": bpp * sc.n / (pk / 1e3) / 1e9 / hbm_gbs}
         del data
     return res
+
+
+def run_c2_leg(make_ctx, timed_frames, hbm_gbs, frames=200):
+    """The 2^22-point 1920x1080 orbit (L2 flushed before every frame), zero
+    copy and host round trip."""
+    sc = inputs.C2
+    stored = inputs.encode(sc.positions(), "f32")
+    ctx = make_ctx("f32", stored, sc)
+    step_ms, _, _ = timed_frames(ctx, sc, frames, 5, True)
+    _, point_ms, resolve_ms = timed_frames(ctx, sc, frames, 3, True, kernel_times=True)
+    rt_ms, _, _ = timed_frames(ctx, sc, 50, 3, True, roundtrip=True)
+    ctx.close()
+    m = statistics.mean(step_ms)
+    pk = statistics.mean(point_ms)
+    return {"ms_per_frame": m, "points_per_s": sc.n / (m / 1e3), "p99_ms": float(np.percentile(step_ms, 99)),
+            "points_kernel_ms": pk, "resolve_ms": statistics.mean(resolve_ms),
+            "points_kernel_frac": 24 * sc.n / (pk / 1e3) / 1e9 / hbm_gbs,
+            "roundtrip_pinned_ms_per_frame": statistics.mean(rt_ms),
+            "zero_copy_vs_roundtrip_pinned": statistics.mean(rt_ms) / m, "frames": frames,
+            "l2": f"flushed before every frame ({FLUSH_BYTES >> 20} MB read)"}
 
 
 def run_features(sc, stored, hbm_gbs, frames=50):
@@ -546,13 +614,21 @@ def run_batched(hbm_gbs, frames=100):
     table = inputs.batched_table()
     clouds = [dict(n=bc.n, width=bc.W, height=bc.H, seed=4, cloud=i, amplitude=5e-4) for i, bc in enumerate(table)]
     stream = torch.cuda.current_stream()
+    starts = {}
     with Batch(clouds, "f32", camera_slots=frames) as b:
         for i, bc in enumerate(table):
-            b.points(i).copy_(torch.from_numpy(inputs.encode(inputs.batch_cloud_positions(bc), "f32")))
+            stored = inputs.encode(inputs.batch_cloud_positions(bc), "f32")
+            if i in BATCH_ACCURACY_CLOUDS:
+                starts[i] = stored
+            b.points(i).copy_(torch.from_numpy(stored))
             for f in range(frames):
                 eye = inputs.orbit_eye(f, bc.deg_per_frame, bc.radius, CENTRE, bc.elevation, bc.start_deg)
                 b.set_camera(i, f, eye, CENTRE, UP, 60.0, 0.1, 100.0)
         torch.cuda.synchronize()
+        # the first frame of a sample of clouds against the FP64 oracle (host side, before any timing)
+        b.step_and_render(stream)
+        torch.cuda.synchronize()
+        fp64 = batch_accuracy(b, table, clouds, starts)
         tuned = b.autotune(frames_per_config=2, stream=stream)
         b.run_graph(3, stream)                                   # warm-up frames
         per_frame = []
@@ -596,8 +672,66 @@ def run_batched(hbm_gbs, frames=100):
                                  "p99_ms": float(np.percentile(rt_ms, 99)), "frames": rt_frames,
                                  "points_per_s": n_pts / (statistics.mean(rt_ms) / 1e3),
                                  "host_bytes_per_frame": 2 * 12 * n_pts},
-            "zero_copy_vs_roundtrip": statistics.mean(rt_ms) / ms,
+            "zero_copy_vs_roundtrip": statistics.mean(rt_ms) / ms, "fp64_error": fp64,
             "launch": "counter resets + one persistent launch (point items, then each cloud's pixel items one resident grid later) + frame counter, replayed as a CUDA graph"}
+
+
+BATCH_ACCURACY_CLOUDS = (0, 1, 2, 3, 64, 128, 192, 255)
+
+
+def batch_accuracy(b, table, clouds, starts):
+    """First batched frame of a sample of clouds against the FP64 oracle:
+    the worst figures over the sample (oracle/accuracy.py)."""
+    from oracle import accuracy
+    reps = {}
+    for i, stored in starts.items():
+        bc, c = table[i], clouds[i]
+        eye = inputs.orbit_eye(0, bc.deg_per_frame, bc.radius, CENTRE, bc.elevation, bc.start_deg)
+        got = b.points(i).cpu().numpy().reshape(-1, 3)
+        rgba = b.frame_rgba(i).cpu().numpy().reshape(-1).view(np.uint32)
+        reps[i] = accuracy.step_accuracy(stored, "f32", got, rgba, c["seed"], c["cloud"], 0, c["amplitude"], eye,
+                                         CENTRE, UP, 60.0, bc.W, bc.H, 0.1, 100.0)
+    vals = list(reps.values())
+    return {"clouds": sorted(reps), "max_rel": max(r["max_rel"] for r in vals),
+            "rms_rel_max": max(r["rms_rel"] for r in vals),
+            "pixels_all_agree_min": min(r["pixels_all_agree"] for r in vals),
+            "pixels_covered_agree_min": min(r["pixels_covered_agree"] for r in vals),
+            "differing_outside_risk": sum(r["differing_outside_risk"] or 0 for r in vals)}
+
+
+def served_accuracy(cfg, shared):
+    """One tick of the serving engine with one 1920x1080 viewer against the
+    FP64 oracle: the shared cloud (step = tick 0) and the viewer's private
+    cloud (step = its frame 0) in one frame, point ids in that order.  Both
+    clouds are drawn in one colour so the frame is the coverage mask."""
+    import torch
+    from oracle import accuracy
+    from paper_2504_20937_b300 import serve
+    from paper_2504_20937_b300.api import Server
+    req = inputs.ViewerRequest(viewer=0, arrival_s=0.0, W=1920, H=1080, frames=1, private_n=200_000,
+                               start_deg=30.0, init_seed=77)
+    private = serve.private_cloud(req, cfg.dtype)
+    with Server(cfg.shared_n, cfg.dtype, cfg.shared_seed, 0, cfg.amplitude, cfg.budget_bytes) as srv:
+        srv.shared_points().copy_(torch.from_numpy(shared))
+        srv.set_shared_color(0xFFFFFFFF)
+        v = srv.add_viewer(req.private_n, req.W, req.H, seed=req.init_seed, cloud=1, amplitude=cfg.amplitude,
+                           color=0xFFFFFFFF)
+        srv.viewer_points(v).copy_(torch.from_numpy(private))
+        eye = serve.viewer_eye(req, 0, cfg)
+        srv.set_camera(v, eye, CENTRE, UP, cfg.fovy_deg, cfg.znear, cfg.zfar)
+        srv.tick()
+        torch.cuda.synchronize()
+        got_shared = srv.shared_points().cpu().numpy().reshape(-1, 3)
+        got_private = srv.viewer_points(v).cpu().numpy().reshape(-1, 3)
+        rgba = srv.frame(v)[0].cpu().numpy().reshape(-1).view(np.uint32)
+    segs = [{"stored_before": shared, "got_after": got_shared, "seed": cfg.shared_seed, "cloud": 0, "step": 0,
+             "amplitude": cfg.amplitude},
+            {"stored_before": private, "got_after": got_private, "seed": req.init_seed, "cloud": 1, "step": 0,
+             "amplitude": cfg.amplitude}]
+    rep = accuracy.segments_accuracy(segs, cfg.dtype, rgba, eye, CENTRE, UP, cfg.fovy_deg, req.W, req.H,
+                                     cfg.znear, cfg.zfar)
+    rep["case"] = f"shared {cfg.shared_n} + private {req.private_n} points, one viewer at {req.W}x{req.H}"
+    return rep
 
 
 def run_served(requests=10_000, roundtrip=True):
@@ -610,11 +744,12 @@ def run_served(requests=10_000, roundtrip=True):
     cfg = serve.ServeConfig()
     shared = inputs.encode(inputs.uniform_cloud(cfg.shared_n, cfg.shared_seed), cfg.dtype)
     clouds = {r.viewer: serve.private_cloud(r, cfg.dtype) for r in trace}
+    fp64 = served_accuracy(cfg, shared) if roundtrip else None
     zero = serve.run_trace(trace, cfg, clouds=clouds, shared=shared).summary()
     rt = serve.run_trace(trace, cfg, roundtrip=True, clouds=clouds, shared=shared).summary() if roundtrip else None
     return {"requests": requests, "viewers": len(trace), "shared_points": cfg.shared_n,
             "max_concurrent": cfg.max_viewers, "budget_gb": cfg.budget_bytes / 2**30,
-            "zero_copy": zero, "roundtrip": rt,
+            "zero_copy": zero, "roundtrip": rt, "fp64_error": fp64,
             "latency_note": "frame latency = completion of the tick that rendered it minus its request time "
                             "(arrival, or the viewer's previous frame); wall clock, host overheads included"}
 
@@ -704,32 +839,30 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     out = run_ours(args, rank, world, local)
     if rank == 0:
-        if args.cpu_frames > 0:
-            sc = scene_for(args.workload, args.points)
-            stored = inputs.encode(sc.positions(), "f32")
-            frames = args.cpu_frames
+        sc = scene_for(args.workload, args.points)
+        frames = args.cpu_frames if args.cpu_frames >= 0 else (6 if sc.n > 1 << 24 else 60)
+        stored = inputs.encode(sc.positions(), "f32") if frames > 0 or args.cpu_omp_seconds > 0 else None
+        if frames > 0:
             rate, dt = cpu_oracle_rate(sc, stored, frames, sc.n)
             out["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": 1, "kind": "oracle",
                                    "sample": f"{frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the "
                                              f"workload on one host core, {dt:.1f} s"}
-        if args.cpu_frames > 0 and not args.no_extra:
-            # the oracle on one core for the other two single-cloud configurations: the whole 100-step
-            # reference run, and three frames of the 64M-point 4K frame (per-frame time)
+        if frames > 0 and not args.no_extra:
+            # the oracle on one core for the other single-cloud configurations: the whole 100-step
+            # reference run, and 20 frames of the other one (per-frame time)
             cfgs = {}
             pr1 = inputs.PR1
             rate, dt = cpu_oracle_rate(pr1, inputs.encode(pr1.positions(), "f32"), pr1.frames, pr1.n)
             cfgs[pr1.name] = {"points_per_s": rate, "seconds": dt, "frames": pr1.frames, "cores": 1}
-            c3 = inputs.C3
-            rate, dt = cpu_oracle_rate(c3, inputs.encode(c3.positions(), "f32"), 3, c3.n)
-            cfgs[c3.name] = {"points_per_s": rate, "ms_per_frame": dt / 3 * 1e3, "frames": 3, "cores": 1}
+            other, of = (inputs.C2, 20) if sc.name != inputs.C2.name else (inputs.C3, 3)
+            rate, dt = cpu_oracle_rate(other, inputs.encode(other.positions(), "f32"), of, other.n)
+            cfgs[other.name] = {"points_per_s": rate, "ms_per_frame": dt / of * 1e3, "frames": of, "cores": 1}
             out["cpu_baseline_configs"] = cfgs
         if args.cpu_omp_seconds > 0:
-            sc = scene_for(args.workload, args.points)
-            stored = inputs.encode(sc.positions(), "f32")
-            rate, dt, frames, threads = cpu_omp_rate(sc, stored, args.cpu_omp_seconds)
+            rate, dt, omp_frames, threads = cpu_omp_rate(sc, stored, args.cpu_omp_seconds)
             out["cpu_baseline_openmp"] = {
                 "value": rate, "unit": "points/s", "cores": threads, "kind": "oracle routines over OpenMP threads",
-                "sample": f"{frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the workload, {dt:.1f} s; "
+                "sample": f"{omp_frames} full frames ({sc.n} points, {sc.W}x{sc.H}) of the workload, {dt:.1f} s; "
                           f"host reports {os.cpu_count()} logical CPUs"}
         print(json.dumps(out), flush=True)
     if world > 1:
