@@ -203,9 +203,10 @@ MMR_API mmr_status mmr_step_and_render_pingpong(mmr_ctx *ctx, void *stream);
  * allocates velocities (3n floats, zero) and masses (n floats, zero; write
  * them), plus scratch for per-chunk sums, and returns the velocity and mass
  * device pointers.  mmr_nbody_step_and_render: for every body i, acc = the
- * sum over j of (p_j - p_i) m_j / (|p_j - p_i|^2 + eps2)^(3/2), taken in
- * chunks of 1024 consecutive j (each chunk in order, then the chunk sums in
- * order; FP32, exact sqrt and division), v += G acc dt, p' = p + v dt
+ * sum over j of (p_j - p_i) m_j / (|p_j - p_i|^2 + eps2)^(3/2) (FP32, exact
+ * sqrt and division), summed in chunks of 1024 consecutive j (each chunk in
+ * order, then the chunk sums in order), which stays within the FP32
+ * summation error bound of the sequential sum; v += G acc dt, p' = p + v dt
  * written to the other buffer, which is then
  * rendered (1-px splat fused into the same kernel) and made visible.  Needs
  * eps2 > 0 (it also removes the j = i term).  Advances the step counter. */

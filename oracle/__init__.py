@@ -55,8 +55,10 @@ _sig("orc_splat_h16", None, _u16p, C.c_int, C.c_uint64, _f32p, C.c_int, C.c_int,
      C.c_uint32, _u64p)
 _sig("orc_splat_disc_f32", None, _f32p, C.c_uint64, _f32p, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
      C.c_uint32, _u64p)
-_sig("orc_nbody_step_f32", None, _f32p, _f32p, _f32p, _f32p, C.c_uint64, C.c_float, C.c_float, C.c_float,
+_sig("orc_nbody_step_f32", None, _f32p, _f32p, _f32p, _f32p, C.c_uint64, C.c_float, C.c_float, C.c_float)
+_sig("orc_nbody_step_f32_chunked", None, _f32p, _f32p, _f32p, _f32p, C.c_uint64, C.c_float, C.c_float, C.c_float,
      C.c_uint64)
+_sig("orc_nbody_abs_term_sums", None, _f32p, _f32p, C.c_uint64, C.c_float, _f64p)
 _sig("orc_nbody_accel_f64", None, _f64p, _f64p, C.c_uint64, C.c_double, C.c_double, _f64p)
 _sig("orc_resolve", None, _u64p, C.c_uint64, C.c_void_p, C.c_uint32, C.c_uint32, _u32p)
 
@@ -225,13 +227,41 @@ def render_disc(pos, M32, W, H, znear, zfar, radius, colors=None, color=0xFFFFFF
 NBODY_CHUNK = 1024
 
 
-def nbody_step_f32(pos, vel, mass, G, eps2, dt, chunk=NBODY_CHUNK):
-    """One all-pairs gravity step (Sec. 4.2.3), terms summed in chunks of
-    `chunk` bodies; returns the new positions, updates vel in place."""
+def nbody_step_f32(pos, vel, mass, G, eps2, dt):
+    """One all-pairs gravity step (Sec. 4.2.3), the terms summed in order of
+    j (the definition); returns the new positions, updates vel in place."""
     out = np.empty_like(pos)
     _lib.orc_nbody_step_f32(np.ascontiguousarray(pos, np.float32).reshape(-1), out.reshape(-1), vel.reshape(-1),
-                            np.ascontiguousarray(mass, np.float32), pos.shape[0], G, eps2, dt, chunk)
+                            np.ascontiguousarray(mass, np.float32), pos.shape[0], G, eps2, dt)
     return out
+
+
+def nbody_step_f32_chunked(pos, vel, mass, G, eps2, dt, chunk=NBODY_CHUNK):
+    """The same step with the terms summed in chunks of `chunk` bodies (each
+    chunk in order, then the chunk sums in order): the rounding order of the
+    GPU kernel, for its bit-for-bit check."""
+    out = np.empty_like(pos)
+    _lib.orc_nbody_step_f32_chunked(np.ascontiguousarray(pos, np.float32).reshape(-1), out.reshape(-1),
+                                    vel.reshape(-1), np.ascontiguousarray(mass, np.float32), pos.shape[0], G, eps2,
+                                    dt, chunk)
+    return out
+
+
+def nbody_abs_term_sums(pos, mass, eps2):
+    """float64[n,3]: sum over j of |t_j| per component of body i's terms."""
+    out = np.zeros((pos.shape[0], 3), np.float64)
+    _lib.orc_nbody_abs_term_sums(np.ascontiguousarray(pos, np.float32).reshape(-1),
+                                 np.ascontiguousarray(mass, np.float32), pos.shape[0], eps2, out.reshape(-1))
+    return out
+
+
+def summation_bound_gamma(n):
+    """Higham's gamma_{n-1} = (n-1)u / (1 - (n-1)u), u = 2^-24: recursive FP32
+    summation of n terms in any order is within gamma_{n-1} sum |t_j| of the
+    exact sum (N. J. Higham, Accuracy and Stability of Numerical Algorithms,
+    2nd ed., SIAM 2002, Sec. 4.2)."""
+    k = max(n - 1, 0) * 2.0**-24
+    return k / (1.0 - k)
 
 
 def nbody_accel_f64(pos, mass, G, eps2):

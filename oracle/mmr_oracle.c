@@ -473,46 +473,102 @@ void orc_splat_disc_f32(const float *pos, uint64_t n, const float M[16], int W, 
 /* gravity; for body i the terms, j = 0 .. n-1,                              */
 /*   d = p_j - p_i,  r2 = ((dx dx + dy dy) + dz dz) + eps2,                  */
 /*   inv = 1 / sqrt(r2),  t_j = d (m_j ((inv inv) inv))   (zero for j = i),  */
-/* are summed in chunks of `chunk` consecutive j: each chunk in order of j   */
-/* from zero, then the chunk sums in chunk order from zero.  (The paper does */
-/* not fix an order; with one chunk this is the plain sequential sum.)       */
-/* Then a = G acc, v' = v + a dt, p' = p + v' dt (semi-implicit Euler).      */
-/* FP32, every operation rounded once, in that order; positions are read    */
-/* from pin and written to pout (two buffers, as the paper's ping-pong).     */
+/* summed in order of j, acc = (..((t_0 + t_1) + t_2) ..) + t_{n-1}.  Then   */
+/* a = G acc, v' = v + a dt, p' = p + v' dt (semi-implicit Euler).  FP32,    */
+/* every operation rounded once, in that order; positions are read from pin */
+/* and written to pout (two buffers, as the paper's ping-pong).              */
 /* ------------------------------------------------------------------------ */
+
+/* One term t_j of body i's sum (shared by the two summation orders below). */
+static void nbody_term(const float *pin, const float *mass, uint64_t j, float px, float py, float pz, float eps2,
+                       float t[3])
+{
+    float dx = pin[3 * j] - px;
+    float dy = pin[3 * j + 1] - py;
+    float dz = pin[3 * j + 2] - pz;
+    float r2 = ((dx * dx + dy * dy) + dz * dz) + eps2;
+    float inv = 1.0f / sqrtf(r2);
+    float s = mass[j] * ((inv * inv) * inv);
+    t[0] = dx * s;
+    t[1] = dy * s;
+    t[2] = dz * s;
+}
+
+/* The update of body i from its summed acceleration (ax, ay, az). */
+static void nbody_update(const float *pin, float *pout, float *vel, uint64_t i, float ax, float ay, float az,
+                         float G, float dt)
+{
+    float vx = vel[3 * i] + (G * ax) * dt;
+    float vy = vel[3 * i + 1] + (G * ay) * dt;
+    float vz = vel[3 * i + 2] + (G * az) * dt;
+    vel[3 * i] = vx;
+    vel[3 * i + 1] = vy;
+    vel[3 * i + 2] = vz;
+    pout[3 * i] = pin[3 * i] + vx * dt;
+    pout[3 * i + 1] = pin[3 * i + 1] + vy * dt;
+    pout[3 * i + 2] = pin[3 * i + 2] + vz * dt;
+}
+
+/* The definition: the plain sequential sum over j. */
 void orc_nbody_step_f32(const float *pin, float *pout, float *vel, const float *mass, uint64_t n, float G,
-                        float eps2, float dt, uint64_t chunk)
+                        float eps2, float dt)
 {
     for (uint64_t i = 0; i < n; ++i) {
         const float px = pin[3 * i], py = pin[3 * i + 1], pz = pin[3 * i + 2];
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        float ax = 0.0f, ay = 0.0f, az = 0.0f, t[3];
+        for (uint64_t j = 0; j < n; ++j) {
+            nbody_term(pin, mass, j, px, py, pz, eps2, t);
+            ax = ax + t[0];
+            ay = ay + t[1];
+            az = az + t[2];
+        }
+        nbody_update(pin, pout, vel, i, ax, ay, az, G, dt);
+    }
+}
+
+/* The same terms summed in another fixed order, the one a GPU kernel uses:  */
+/* chunks of `chunk` consecutive j, each chunk in order of j from zero, then */
+/* the chunk sums in chunk order from zero.  With one chunk it is the        */
+/* sequential sum above.  This is not a second definition: it replays the    */
+/* kernel's rounding order so the kernel can be checked bit for bit, while   */
+/* the kernel is held to the sequential sum by a summation error bound.      */
+void orc_nbody_step_f32_chunked(const float *pin, float *pout, float *vel, const float *mass, uint64_t n, float G,
+                                float eps2, float dt, uint64_t chunk)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        const float px = pin[3 * i], py = pin[3 * i + 1], pz = pin[3 * i + 2];
+        float ax = 0.0f, ay = 0.0f, az = 0.0f, t[3];
         for (uint64_t c0 = 0; c0 < n; c0 += chunk) {
             const uint64_t c1 = c0 + chunk < n ? c0 + chunk : n;
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
             for (uint64_t j = c0; j < c1; ++j) {
-                float dx = pin[3 * j] - px;
-                float dy = pin[3 * j + 1] - py;
-                float dz = pin[3 * j + 2] - pz;
-                float r2 = ((dx * dx + dy * dy) + dz * dz) + eps2;
-                float inv = 1.0f / sqrtf(r2);
-                float s = mass[j] * ((inv * inv) * inv);
-                sx = sx + dx * s;
-                sy = sy + dy * s;
-                sz = sz + dz * s;
+                nbody_term(pin, mass, j, px, py, pz, eps2, t);
+                sx = sx + t[0];
+                sy = sy + t[1];
+                sz = sz + t[2];
             }
             ax = ax + sx;
             ay = ay + sy;
             az = az + sz;
         }
-        float vx = vel[3 * i] + (G * ax) * dt;
-        float vy = vel[3 * i + 1] + (G * ay) * dt;
-        float vz = vel[3 * i + 2] + (G * az) * dt;
-        vel[3 * i] = vx;
-        vel[3 * i + 1] = vy;
-        vel[3 * i + 2] = vz;
-        pout[3 * i] = px + vx * dt;
-        pout[3 * i + 1] = py + vy * dt;
-        pout[3 * i + 2] = pz + vz * dt;
+        nbody_update(pin, pout, vel, i, ax, ay, az, G, dt);
+    }
+}
+
+/* Sum over j of |t_j| per component, in FP64 from the FP32 terms (the      */
+/* magnitudes a summation error bound scales with).                          */
+void orc_nbody_abs_term_sums(const float *pin, const float *mass, uint64_t n, float eps2, double *out)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        double a[3] = { 0.0, 0.0, 0.0 };
+        float t[3];
+        for (uint64_t j = 0; j < n; ++j) {
+            nbody_term(pin, mass, j, pin[3 * i], pin[3 * i + 1], pin[3 * i + 2], eps2, t);
+            for (int k = 0; k < 3; ++k)
+                a[k] += fabs((double)t[k]);
+        }
+        for (int k = 0; k < 3; ++k)
+            out[3 * i + k] = a[k];
     }
 }
 

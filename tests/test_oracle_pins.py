@@ -483,6 +483,32 @@ def test_nbody_two_body_closed_form():
     assert out[0, 0] == pytest.approx(a * dt * dt, rel=1e-5) and out[1, 0] == pytest.approx(d - a * dt * dt, rel=1e-6)
 
 
+def nbody_velocity_tolerance(S, v_new, v_old, G, dt, n):
+    """Largest difference of v' = v + (G acc) dt between two summation orders
+    of acc: each order is within gamma_{n-1} S of the exact sum (Higham,
+    Sec. 4.2), so the two accelerations differ by at most 2 gamma_{n-1} S; the
+    three roundings after the sum add at most u (|x| + |y|) each, taken here
+    as 8u (|v_old| + |v_new| + |G dt| S) with margin."""
+    u = 2.0**-24
+    g = oracle.summation_bound_gamma(n)
+    return abs(G * dt) * 2.0 * g * S * (1 + 4 * u) + 8 * u * (np.abs(v_old) + np.abs(v_new) + abs(G * dt) * S)
+
+
+def test_nbody_summation_bound_catches_a_dropped_term():
+    """The tolerance above is tight enough to see a whole term go missing for
+    a body that one close neighbour dominates."""
+    pos = np.array([[0.5, 0.5, 0.5], [0.5005, 0.5, 0.5], [0.9, 0.1, 0.2], [0.1, 0.8, 0.3]], np.float32)
+    mass = np.ones(4, np.float32)
+    G, eps2, dt = np.float32(1e-3), np.float32(1e-6), np.float32(1e-2)
+    vel = np.zeros_like(pos)
+    oracle.nbody_step_f32(pos, vel, mass, G, eps2, dt)
+    vel_missing = np.zeros_like(pos)
+    oracle.nbody_step_f32(pos[:3], vel_missing[:3], mass[:3], G, eps2, dt)     # body 3's pull dropped
+    S = oracle.nbody_abs_term_sums(pos, mass, float(eps2))
+    tol = nbody_velocity_tolerance(S, vel, np.zeros_like(vel), float(G), float(dt), 4)
+    assert np.any(np.abs(vel_missing[:3].astype(np.float64) - vel[:3]) > tol[:3])
+
+
 def test_nbody_matches_fp64_brute_force_and_conserves_momentum():
     n = 300
     rng = np.random.default_rng(8)
@@ -498,13 +524,17 @@ def test_nbody_matches_fp64_brute_force_and_conserves_momentum():
     acc_np = float(G) * (d * (mass.astype(np.float64)[None, :] / r2 ** 1.5)[..., None]).sum(1)
     assert np.allclose(acc64, acc_np, rtol=1e-12, atol=1e-15)
     assert np.allclose(vel / float(dt), acc64, rtol=2e-4, atol=1e-6)
-    # the chunked order stays within FP32 rounding of the plain sequential sum
-    vel_seq = np.zeros_like(pos)
-    oracle.nbody_step_f32(pos, vel_seq, mass, G, eps2, dt, chunk=n)
-    vel_chunked = np.zeros_like(pos)
-    oracle.nbody_step_f32(pos, vel_chunked, mass, G, eps2, dt, chunk=7)
-    assert np.allclose(vel_chunked, vel_seq, rtol=1e-4, atol=1e-9)
-    assert not np.array_equal(vel_chunked, vel_seq)       # a different, but fixed, rounding order
+    # one chunk is the sequential sum itself; other chunkings stay within the summation error bound of it
+    vel_one = np.zeros_like(pos)
+    oracle.nbody_step_f32_chunked(pos, vel_one, mass, G, eps2, dt, chunk=n)
+    assert np.array_equal(vel_one, vel)
+    S = oracle.nbody_abs_term_sums(pos, mass, float(eps2))
+    for chunk in (7, 64, 150):
+        vel_chunked = np.zeros_like(pos)
+        oracle.nbody_step_f32_chunked(pos, vel_chunked, mass, G, eps2, dt, chunk=chunk)
+        assert not np.array_equal(vel_chunked, vel)       # a different, but fixed, rounding order
+        tol = nbody_velocity_tolerance(S, vel, np.zeros_like(vel), float(G), float(dt), n)
+        assert np.all(np.abs(vel_chunked.astype(np.float64) - vel) <= tol)
     # pairwise forces cancel: total momentum stays at zero up to FP32 rounding
     p_tot = (mass[:, None].astype(np.float64) * vel.astype(np.float64)).sum(0)
     scale = (mass[:, None] * np.abs(vel)).sum(0)
