@@ -167,14 +167,39 @@ MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t backgrou
  *    one thread per group, ctas_per_sm > 0 a persistent grid of
  *    sm_count * ctas_per_sm CTAs.  On FP32 storage every thread of such a
  *    grid prefetches its next group while working on the current one; the
- *    16-bit kernels load each group when they reach it, to stay at 48
- *    registers.
+ *    16-bit kernels load each group when they reach it, to stay at 40
+ *    registers.  Each point reads its pixel's key and, when it is nearer,
+ *    takes a 64-bit atomic minimum.
  *  kernel = MMR_KERNEL_TMA: persistent, TMA-staged (threads 128, 256 or
  *    512; ctas_per_sm >= 1): each CTA keeps 4 tiles of threads*48 bytes in
  *    flight through shared memory with bulk copies.
- * Results never depend on the shape; only speed does.  The default is the
- * fastest shape measured on B300 (see the library's design notes). */
-enum mmr_kernel { MMR_KERNEL_GRID = 0, MMR_KERNEL_TMA = 1 };
+ *  kernel = MMR_KERNEL_DEPTH_BOUND: the grid-stride kernel in two passes
+ *    over the points with screen-tile depth bounds between them, for dense
+ *    clouds: the first eighth of the point groups splats as usual and marks
+ *    the 8x8-pixel tiles it wrote; a small kernel takes the largest depth of
+ *    each marked tile's keys; the rest of the points skip the depth-buffer
+ *    read when they lie behind their tile's bound (they could not win any of
+ *    its pixels).  Three point-phase launches; 16 bytes per tile of device
+ *    memory, allocated at the first such frame.
+ *  kernel = MMR_KERNEL_WARP_AGG: the grid-stride kernel whose lanes that hit
+ *    the same pixel in one step elect their nearest point, which alone reads
+ *    the key and takes the atomic.
+ *  kernel = MMR_KERNEL_AUTO (the default): MMR_KERNEL_DEPTH_BOUND when the
+ *    cloud has at least 2^20 points and four points per pixel, else
+ *    MMR_KERNEL_GRID (64 threads, one thread per group).
+ * Disc markers (mmr_set_marker) use their own grid-stride kernel (64
+ * threads).  Under MMR_KERNEL_DEPTH_BOUND, or MMR_KERNEL_AUTO with at least
+ * 2^20 points and 16 discs over each pixel on average (n pi r^2 >= 16 w h),
+ * it runs in two passes with depth bounds of 32x32-pixel tiles between them:
+ * a later disc behind the bounds of every tile it touches is skipped.
+ * Results never depend on the shape or the kernel; only speed does. */
+enum mmr_kernel {
+    MMR_KERNEL_GRID = 0,
+    MMR_KERNEL_TMA = 1,
+    MMR_KERNEL_DEPTH_BOUND = 2,
+    MMR_KERNEL_WARP_AGG = 3,
+    MMR_KERNEL_AUTO = 4
+};
 MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel);
 
 /* ---- frames ---------------------------------------------------------------- */
@@ -236,6 +261,10 @@ MMR_API mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int
  * synchronised, until the next frame or mmr_destroy.  Either output pointer
  * may be NULL. */
 MMR_API mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **depth_id);
+
+/* Number of kernels the latest frame of this context launched (point phase
+ * and resolve), for launch counting in benchmarks. */
+MMR_API mmr_status mmr_last_frame_kernels(const mmr_ctx *ctx, int *kernels);
 
 /* Current step counter (index of the next displacement step). */
 MMR_API mmr_status mmr_get_step(const mmr_ctx *ctx, uint32_t *step);

@@ -44,6 +44,12 @@ REL_FLOOR = 2.0**-14
 # is a fivefold margin.
 FP32_PROJECTION_SLACK_PX = 0.01
 
+# Largest half-width (pixels) of a screen box the at-risk check handles; a box
+# narrower than 2h touches at most 2h + 1 pixels per axis, all of which it
+# marks.  Binary16 boxes at 3840x2160 reach about 0.7 px; bfloat16 ones are
+# eight times wider and fall outside the check.
+MAX_HALF_BOX_PX = 1.5
+
 
 def coordinate_bound(p_ref: np.ndarray, dtype: str, amplitude: float) -> np.ndarray:
     """Bound on |x_gpu - x_ref| per coordinate after one step of the given
@@ -66,8 +72,8 @@ def relative_error(got: np.ndarray, ref: np.ndarray) -> dict:
 def at_risk_pixels(p_ref: np.ndarray, eps: np.ndarray, M64: np.ndarray, W: int, H: int, znear: float,
                    zfar: float, chunk: int = 1 << 23):
     """(may, must): boolean W*H masks, or None when some point's screen box
-    is a pixel wide or more (then it can touch more than two pixels per axis
-    and this check does not apply).  `must` marks pixels that a point's
+    has a half-width of MAX_HALF_BOX_PX or more (the check then does not
+    apply).  `must` marks pixels that a point's
     whole screen box lies in (covered in both frames); `may` marks every
     pixel a box touches.  A pixel outside `may` is empty in both frames.
 
@@ -99,14 +105,18 @@ def at_risk_pixels(p_ref: np.ndarray, eps: np.ndarray, M64: np.ndarray, W: int, 
             dy = 0.5 * H * (ay * cwa + np.abs(cy) * aw) / den + FP32_PROJECTION_SLACK_PX
             sx = 0.5 * W * (1.0 + cx / cw)
             sy = 0.5 * H * (1.0 - cy / cw)
-        good = maybe & (cwa > aw) & np.isfinite(dx) & np.isfinite(dy) & (dx < 0.5) & (dy < 0.5)
+        good = maybe & (cwa > aw) & np.isfinite(dx) & np.isfinite(dy) & (dx < MAX_HALF_BOX_PX) & \
+            (dy < MAX_HALF_BOX_PX)
         if np.any(maybe & ~good):
-            return None          # a box may span more than two pixels: this check does not apply
+            return None          # a box may span more pixels than this check walks: it does not apply
         x0, x1 = np.floor(sx - dx), np.floor(sx + dx)
         y0, y1 = np.floor(sy - dy), np.floor(sy + dy)
-        for xs, ys in ((x0, y0), (x1, y0), (x0, y1), (x1, y1)):
-            inside = good & (xs >= 0) & (xs < W) & (ys >= 0) & (ys < H)
-            may[(ys[inside] * W + xs[inside]).astype(np.int64)] = True
+        span = int(2 * MAX_HALF_BOX_PX) + 1          # a box narrower than 2h spans at most 2h + 1 pixels
+        for ox in range(span):
+            for oy in range(span):
+                xs, ys = x0 + ox, y0 + oy
+                inside = good & (xs <= x1) & (ys <= y1) & (xs >= 0) & (xs < W) & (ys >= 0) & (ys < H)
+                may[(ys[inside] * W + xs[inside]).astype(np.int64)] = True
         whole = good & ok & (x0 == x1) & (y0 == y1) & (x0 >= 0) & (x0 < W) & (y0 >= 0) & (y0 < H)
         must[(y0[whole] * W + x0[whole]).astype(np.int64)] = True
     return may, must

@@ -17,6 +17,7 @@ MMR_OK = 0
 STATUS = {0: "MMR_OK", -1: "MMR_ERR_INVALID_ARG", -2: "MMR_ERR_OOM", -3: "MMR_ERR_BUDGET",
           -4: "MMR_ERR_CUDA", -5: "MMR_ERR_STATE", -6: "MMR_ERR_TIMEOUT"}
 DTYPE_CODE = {"f32": 0, "f16": 1, "bf16": 2}
+KERNEL_CODE = {"grid": 0, "tma": 1, "depth_bound": 2, "warp_agg": 3, "auto": 4}
 
 _vp = C.c_void_p
 _u64 = C.c_uint64
@@ -56,6 +57,7 @@ SIGNATURES = {
     "mmr_step_and_render_roundtrip": (_i, [_vp, _vp, _i]),
     "mmr_frame_ptr": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
     "mmr_get_step": (_i, [_vp, C.POINTER(_u32)]),
+    "mmr_last_frame_kernels": (_i, [_vp, C.POINTER(_i)]),
     "mmr_set_timing": (_i, [_vp, _i]),
     "mmr_check_device": (_i, [_vp]),
     "mmr_selftest_bounded_wait": (_i, [_vp, C.c_longlong, _vp]),

@@ -154,10 +154,14 @@ class Context:
         """0: 1-px points; 0.5..64: disc markers of that radius in pixels."""
         self._check(self._lib.mmr_set_marker(self._h, radius_px))
 
-    def set_launch(self, threads: int = 256, ctas_per_sm: int = 0, kernel: int = 0):
-        """kernel 0: grid-stride (ctas_per_sm 0 = one thread per group, else
-        persistent with prefetch); kernel 1: TMA-staged persistent."""
-        self._check(self._lib.mmr_set_launch(self._h, threads, ctas_per_sm, kernel))
+    def set_launch(self, threads: int = 64, ctas_per_sm: int = 0, kernel=0):
+        """kernel (a code or a name of _lib.KERNEL_CODE): 0 "grid" grid-stride
+        (ctas_per_sm 0 = one thread per group, else persistent with
+        prefetch); 1 "tma" TMA-staged persistent; 2 "depth_bound" two passes
+        with screen-tile depth bounds; 3 "warp_agg" warp-aggregated splat;
+        4 "auto" depth bounds for dense clouds, else grid-stride."""
+        code = _lib.KERNEL_CODE[kernel] if isinstance(kernel, str) else int(kernel)
+        self._check(self._lib.mmr_set_launch(self._h, threads, ctas_per_sm, code))
 
     # -- frames
     def step_and_render(self, stream=None):
@@ -203,6 +207,12 @@ class Context:
         a, b = C.c_float(), C.c_float()
         self._check(self._lib.mmr_last_kernel_ms(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def last_frame_kernels(self) -> int:
+        """Kernels the latest frame launched (point phase and resolve)."""
+        k = C.c_int()
+        self._check(self._lib.mmr_last_frame_kernels(self._h, C.byref(k)))
+        return k.value
 
     @property
     def step(self) -> int:

@@ -11,7 +11,9 @@
 #include "../../include/mmr.h"
 #include "mmr_device.cuh"
 #include "mmr_internal.h"
+#include "mmr_disc.cuh"
 #include "mmr_resolve.cuh"
+#include "mmr_tiles.cuh"
 
 namespace {
 
@@ -44,6 +46,14 @@ struct mmr_ctx {
     uint32_t *index = nullptr;           // indexed colour: colormap[index[id]]
     uint32_t *colormap = nullptr;
     uint32_t ncolors = 0;
+
+    // screen-tile depth bounds (MMR_KERNEL_DEPTH_BOUND), allocated on first use: one block of
+    // 16 bytes per 8x8 tile (mark, list, bound) plus the list's count
+    unsigned char *tiles_mem = nullptr;
+    uint64_t tiles = 0;
+    uint32_t tiles_w = 0;
+    uint32_t tile_tag = 0;
+    int last_frame_kernels = 0;    // kernels the latest frame launched
 
     // round-trip baseline buffers (allocated on first use)
     void *rt_device = nullptr;
@@ -178,23 +188,118 @@ mmr_status check_frame_ready(mmr_ctx *c, bool need_cam)
 
 bool uses_tma(const mmr::LaunchShape &ls) { return ls.kernel == MMR_KERNEL_TMA; }
 
-// The TMA-staged persistent kernel when the launch shape allows it (the
-// context's buffers are padded to whole groups), else the grid-stride one.
+uint64_t tile_bytes(uint64_t tiles) { return 16 * tiles + 16; }
+
+// The depth-bound paths pay where many points share each pixel: for 1-px
+// points at least four points per pixel on average, for disc markers at
+// least kDiscCoverMin discs over each pixel (n pi r^2 / pixels), and a cloud
+// of at least 2^20 points (smaller clouds are launch-bound).
+constexpr double kDiscCoverMin = 16.0;
+
+bool uses_depth_bound(const mmr_ctx *c)
+{
+    if (c->launch.kernel == MMR_KERNEL_DEPTH_BOUND)
+        return true;
+    if (c->launch.kernel != MMR_KERNEL_AUTO || c->n < (1ull << 20))
+        return false;
+    if (c->disc_r > 0.0f)
+        return (double)c->n * 3.14159265358979 * c->disc_r * c->disc_r >= kDiscCoverMin * (double)frame_px(c);
+    return c->n >= 4 * frame_px(c);
+}
+
+// The tile arrays of the depth-bound path, allocated (zero-filled: no tile
+// marked, no bound, an empty list) the first time a frame needs them.
+mmr_status ensure_tiles(mmr_ctx *c)
+{
+    if (c->tiles_mem)
+        return MMR_OK;
+    const uint64_t tw = ((uint64_t)c->W + 7) / 8, th = ((uint64_t)c->H + 7) / 8;
+    mmr_status st = dev_alloc(c, (void **)&c->tiles_mem, tile_bytes(tw * th), "tile depth bounds");
+    if (st != MMR_OK)
+        return st;
+    cudaError_t e = cudaMemset(c->tiles_mem, 0, tile_bytes(tw * th));
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dev_free(c, (void **)&c->tiles_mem, tile_bytes(tw * th));
+        return cuda_fail(c, e, "clearing the tile depth bounds");
+    }
+    c->tiles = tw * th;
+    c->tiles_w = (uint32_t)tw;
+    c->tile_tag = 0;
+    return MMR_OK;
+}
+
+// This frame's view of the tile arrays, with a fresh tag.  Tags run 1, 2, ...;
+// when the 32-bit tag wraps the arrays are cleared on the stream, so no entry
+// of an earlier frame can carry the new tag.
+mmr::TileBounds next_tile_bounds(mmr_ctx *c, cudaStream_t s, cudaError_t *e)
+{
+    *e = cudaSuccess;
+    if (++c->tile_tag == 0) {
+        *e = cudaMemsetAsync(c->tiles_mem, 0, tile_bytes(c->tiles), s);
+        c->tile_tag = 1;
+    }
+    mmr::TileBounds T{};
+    T.mark = reinterpret_cast<uint32_t *>(c->tiles_mem);
+    T.list = T.mark + c->tiles;
+    T.bound = reinterpret_cast<unsigned long long *>(c->tiles_mem + 8 * c->tiles);
+    T.count = reinterpret_cast<uint32_t *>(c->tiles_mem + 16 * c->tiles);
+    T.tag = c->tile_tag;
+    T.tiles_w = c->tiles_w;
+    return T;
+}
+
+// The point phase of a frame: the disc kernel for disc markers, the TMA-staged
+// persistent kernel or the depth-bounded passes when chosen, else the
+// grid-stride kernel (direct or warp-aggregated splat).  Sets the number of
+// kernels launched.
 cudaError_t launch_point_kernel(mmr_ctx *c, const void *src, void *dst, const mmr::PointParams &P, bool displace,
                                 bool splat, cudaStream_t s)
 {
-    if (splat && c->disc_r > 0.0f)
-        return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, s);
+    c->last_frame_kernels = 1;
+    if (splat && c->disc_r > 0.0f) {
+        if (uses_depth_bound(c) && c->tiles_mem) {
+            cudaError_t e;
+            const mmr::TileBounds fine = next_tile_bounds(c, s, &e);
+            if (e != cudaSuccess)
+                return e;
+            // the 32x32-tile bounds live in the fine tiles' bound array, which is more than large enough
+            mmr::DiscBounds T{fine.bound, fine.tag, (uint32_t)((c->W + 31) / 32), (uint32_t)((c->H + 31) / 32)};
+            c->last_frame_kernels = 3;
+            return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, &T, c->launch.bound_shift,
+                                           c->launch.sm_count, s);
+        }
+        return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, nullptr, 0,
+                                       c->launch.sm_count, s);
+    }
     if (uses_tma(c->launch))
         return mmr::launch_points_tma(c->dtype, src, dst, (uint32_t)c->n, P, displace, splat, c->d_err, c->launch,
                                       s);
-    return mmr::launch_points(c->dtype, src, dst, (uint32_t)c->n, P, displace, splat, c->launch, s);
+    if (splat && uses_depth_bound(c) && c->tiles_mem) {
+        cudaError_t e;
+        const mmr::TileBounds T = next_tile_bounds(c, s, &e);
+        if (e != cudaSuccess)
+            return e;
+        c->last_frame_kernels = 3;
+        return mmr::launch_points_bounded(c->dtype, src, dst, (uint32_t)c->n, P, displace, T, (uint32_t)c->tiles,
+                                          c->launch, s);
+    }
+    mmr::LaunchShape ls = c->launch;
+    if (ls.kernel != MMR_KERNEL_WARP_AGG)
+        ls.kernel = MMR_KERNEL_GRID;
+    return mmr::launch_points(c->dtype, src, dst, (uint32_t)c->n, P, displace, splat, ls, s);
 }
 
 // Render the positions in `src` into the splat key buffer (displacing them
 // into `dst` first when `displace`), then resolve and flip key buffers.
 mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStream_t s)
 {
+    if (uses_depth_bound(c)) {
+        mmr_status st = ensure_tiles(c);
+        if (st != MMR_OK)
+            return st;
+    }
     mmr::PointParams P = point_params(c);
     if (c->timing)
         cudaEventRecord(c->ev[0], s);
@@ -212,6 +317,7 @@ mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStre
         cudaEventRecord(c->ev[2], s);
         c->timed_frame = true;
     }
+    c->last_frame_kernels += 1;
     c->latest_buf = cur;
     c->splat_buf = cur ^ 1;
     if (displace)
@@ -305,7 +411,7 @@ mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx *
     c->budget = budget_bytes;
     c->launch.threads = 64;           // fastest measured shape (grid-stride, one thread per group)
     c->launch.ctas_per_sm = 0;
-    c->launch.kernel = MMR_KERNEL_GRID;
+    c->launch.kernel = MMR_KERNEL_AUTO;   // depth bounds for dense clouds, else the grid-stride kernel
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&c->launch.sm_count, cudaDevAttrMultiProcessorCount, c->device);
@@ -366,6 +472,7 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     dev_free(ctx, (void **)&ctx->nb_partial, (uint64_t)mmr::nbody_chunks((uint32_t)ctx->n) * ctx->n * 16);
     dev_free(ctx, (void **)&ctx->colormap, (uint64_t)ctx->ncolors * 4);
     dev_free(ctx, &ctx->rt_device, storage_bytes(ctx->n, ctx->dtype));
+    dev_free(ctx, (void **)&ctx->tiles_mem, tile_bytes(ctx->tiles));
     if (ctx->rt_host) {
         if (ctx->rt_host_pinned == 1)
             cudaFreeHost(ctx->rt_host);
@@ -675,7 +782,7 @@ mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel
     if (threads < 32 || threads > 1024 || threads % 32 != 0 || ctas_per_sm < 0 || ctas_per_sm > 64)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: threads %d / ctas_per_sm %d out of range",
                     threads, ctas_per_sm);
-    if (kernel != MMR_KERNEL_GRID && kernel != MMR_KERNEL_TMA)
+    if (kernel < MMR_KERNEL_GRID || kernel > MMR_KERNEL_AUTO)
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: unknown kernel %d", kernel);
     if (kernel == MMR_KERNEL_TMA && (ctas_per_sm < 1 || (threads != 128 && threads != 256 && threads != 512)))
         return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_launch: the TMA kernel needs 128/256/512 threads and "
@@ -788,6 +895,14 @@ mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **d
         *rgba = ctx->rgba;
     if (depth_id)
         *depth_id = reinterpret_cast<const uint64_t *>(ctx->keys[ctx->latest_buf]);
+    return MMR_OK;
+}
+
+mmr_status mmr_last_frame_kernels(const mmr_ctx *ctx, int *kernels)
+{
+    if (!ctx || !kernels)
+        return MMR_ERR_INVALID_ARG;
+    *kernels = ctx->last_frame_kernels;
     return MMR_OK;
 }
 

@@ -19,14 +19,26 @@ namespace mmr {
 // computed interval still holds every pixel that can pass; a point farther
 // out is more than 2^17 pixels from any frame (width <= 32768) and its
 // interval is empty either way.  NaN bounds convert to 0 and fail the test.
-__device__ __forceinline__ void splat_disc(float sx, float sy, unsigned long long key, const PointParams &P)
+struct DiscBox {
+    int x0, x1, y0, y1;      // candidate columns x0..x1 and rows y0..y1 (empty when x0 > x1 or y0 > y1)
+};
+
+__device__ __forceinline__ DiscBox disc_box(float sx, float sy, const PointParams &P)
 {
     constexpr float kMargin = 0.0625f;
     const float cx = __fsub_rn(sx, 0.5f), cy = __fsub_rn(sy, 0.5f);
-    const int x0 = max(__float2int_ru(__fsub_rn(__fsub_rn(cx, P.disc_r), kMargin)), 0);
-    const int x1 = min(__float2int_rd(__fadd_rn(__fadd_rn(cx, P.disc_r), kMargin)), P.W - 1);
-    const int y0 = max(__float2int_ru(__fsub_rn(__fsub_rn(cy, P.disc_r), kMargin)), 0);
-    const int y1 = min(__float2int_rd(__fadd_rn(__fadd_rn(cy, P.disc_r), kMargin)), P.H - 1);
+    DiscBox b;
+    b.x0 = max(__float2int_ru(__fsub_rn(__fsub_rn(cx, P.disc_r), kMargin)), 0);
+    b.x1 = min(__float2int_rd(__fadd_rn(__fadd_rn(cx, P.disc_r), kMargin)), P.W - 1);
+    b.y0 = max(__float2int_ru(__fsub_rn(__fsub_rn(cy, P.disc_r), kMargin)), 0);
+    b.y1 = min(__float2int_rd(__fadd_rn(__fadd_rn(cy, P.disc_r), kMargin)), P.H - 1);
+    return b;
+}
+
+__device__ __forceinline__ void splat_disc(float sx, float sy, unsigned long long key, const PointParams &P,
+                                           const DiscBox &box)
+{
+    const int x0 = box.x0, x1 = box.x1, y0 = box.y0, y1 = box.y1;
     // Candidates go four at a time: their tests, then their four depth reads
     // together, then the compares and atomics.  One at a time, each read would
     // wait for the previous pixel's atomic (the compiler cannot move a read
@@ -50,6 +62,63 @@ __device__ __forceinline__ void splat_disc(float sx, float sy, unsigned long lon
                 if (in[k] && key < cur[k])
                     atomicMin(row + px + k, key);
         }
+    }
+}
+
+__device__ __forceinline__ void splat_disc(float sx, float sy, unsigned long long key, const PointParams &P)
+{
+    splat_disc(sx, sy, key, P, disc_box(sx, sy, P));
+}
+
+// Depth bounds for disc markers, on 32x32-pixel tiles of the whole frame:
+// after a first pass over a slice of the points, disc_tile_bound_body stores
+// for every tile the largest depth bits of its keys (all ones when a pixel
+// is still empty), tagged with the frame's tag.  A later disc whose depth
+// bits exceed the bound of every tile its candidate box touches would lose
+// on every pixel it covers (each of them lies in one of those tiles, whose
+// keys only decrease), so it is skipped whole.
+constexpr int kDiscTileShift = 5;
+
+struct DiscBounds {
+    unsigned long long *bound;  // per tile: (tag << 32) | largest depth bits
+    uint32_t tag;               // this frame's tag (never 0)
+    uint32_t tiles_w, tiles_h;
+};
+
+__device__ __forceinline__ bool disc_behind_bounds(const DiscBox &b, uint32_t depth_bits, const DiscBounds &T)
+{
+    if (b.x0 > b.x1 || b.y0 > b.y1)
+        return true;                                     // covers no pixel of the frame
+    for (int ty = b.y0 >> kDiscTileShift; ty <= (b.y1 >> kDiscTileShift); ++ty)
+        for (int tx = b.x0 >> kDiscTileShift; tx <= (b.x1 >> kDiscTileShift); ++tx) {
+            const unsigned long long v = __ldca(T.bound + (uint32_t)ty * T.tiles_w + (uint32_t)tx);
+            if ((uint32_t)(v >> 32) != T.tag || depth_bits <= (uint32_t)v)
+                return false;
+        }
+    return true;
+}
+
+// One warp per tile, grid-stride over all tiles: lane l takes column l of
+// each of the tile's rows.  Pixels outside the frame are left out: no disc
+// reaches them (candidate boxes are clipped to the frame), and every tile
+// holds at least one pixel of the frame.
+__device__ __forceinline__ void disc_tile_bound_body(const unsigned long long *__restrict__ keys, int W, int H,
+                                                     const DiscBounds &T)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t tiles = T.tiles_w * T.tiles_h;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += warps) {
+        const uint32_t x = (t % T.tiles_w) * 32u + lane;
+        const uint32_t y0 = (t / T.tiles_w) * 32u;
+        const uint32_t y1 = min(y0 + 32u, (uint32_t)H);
+        uint32_t m = 0u;
+        if (x < (uint32_t)W)
+            for (uint32_t y = y0; y < y1; ++y)
+                m = max(m, (uint32_t)(__ldcg(keys + (uint64_t)y * (uint32_t)W + x) >> 32));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0)
+            T.bound[t] = ((unsigned long long)T.tag << 32) | m;
     }
 }
 

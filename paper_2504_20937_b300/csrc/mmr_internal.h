@@ -18,12 +18,22 @@ struct NvtxRange {
 
 struct PointParams;
 struct Palette;
+struct TileBounds;
+
+// Point-kernel variants (the values of mmr_set_launch's `kernel`).
+enum : int {
+    kKernelGrid = 0,         // grid-stride, direct depth-tested splat
+    kKernelTma = 1,          // persistent, TMA-staged
+    kKernelDepthBound = 2,   // grid-stride in two passes with per-tile depth bounds (mmr_tiles.cuh)
+    kKernelWarpAgg = 3,      // grid-stride, warp-aggregated splat
+};
 
 struct LaunchShape {
     int threads = 256;       // threads per block
     int ctas_per_sm = 0;     // 0: one thread per work item; else a persistent grid
     int sm_count = 148;
-    int kernel = 0;          // 0: grid-stride point kernel, 1: TMA-staged
+    int kernel = kKernelGrid;
+    int bound_shift = 3;     // depth-bound variant: the first pass takes groups >> bound_shift groups
 };
 
 // Point kernels read positions from src and write displaced ones to dst
@@ -31,9 +41,21 @@ struct LaunchShape {
 cudaError_t launch_points(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
                           bool splat, const LaunchShape &ls, cudaStream_t s);
 
-// Disc markers of radius P.disc_r pixels (grid-stride, 64 threads).
+// Depth-bounded point phase (kKernelDepthBound): the first
+// groups >> ls.bound_shift point groups with the marking splat, the bounds of
+// the marked tiles, the remaining groups with the bounded splat; three
+// launches.  `tiles` is the number of tiles of the frame (the list's size).
+cudaError_t launch_points_bounded(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                                  bool displace, const TileBounds &T, uint32_t tiles, const LaunchShape &ls,
+                                  cudaStream_t s);
+
+// Disc markers of radius P.disc_r pixels (grid-stride, 64 threads).  With
+// T, in two passes around the depth bounds of T's 32x32 tiles: the first
+// groups >> bound_shift groups, the bounds of every tile, then the other
+// groups with discs behind their tiles' bounds skipped; three launches.
+struct DiscBounds;
 cudaError_t launch_points_disc(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
-                               bool displace, cudaStream_t s);
+                               bool displace, const DiscBounds *T, int bound_shift, int sm_count, cudaStream_t s);
 
 // TMA-staged persistent variant (threads 128, 256 or 512; grid =
 // sm_count * ctas_per_sm CTAs).  The buffer must be padded to whole 48-byte

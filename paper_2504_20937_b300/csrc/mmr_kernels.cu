@@ -2,6 +2,7 @@
 // points (grid-stride over 48-byte point groups), and resolve + clear over
 // the pixels.
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -10,28 +11,30 @@
 #include "mmr_internal.h"
 #include "mmr_points.cuh"
 #include "mmr_resolve.cuh"
+#include "mmr_tiles.cuh"
 #include "mmr_tma.cuh"
 
 namespace mmr {
 
-// Grid-stride over 48-byte point groups.  On FP32 storage each thread
-// prefetches its next group into registers before working on the current
-// one, so a load is always in flight while the thread computes.  Positions
-// are read from src and the displaced ones written to dst: the same buffer
-// for an in-place step, the other ping-pong buffer otherwise.
-template <int DT, bool kDisplace, bool kSplat>
-__device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t n, const PointParams &P)
+// Grid-stride over the 48-byte point groups g_begin .. g_end - 1.  On FP32
+// storage each thread prefetches its next group into registers before working
+// on the current one, so a load is always in flight while the thread computes.
+// Positions are read from src and the displaced ones written to dst: the same
+// buffer for an in-place step, the other ping-pong buffer otherwise.  Groups
+// at or past n / G hold the ragged tail (only the last group can).
+template <int DT, bool kDisplace, bool kSplat, typename Splat>
+__device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t n, uint32_t g_begin,
+                                            uint32_t g_end, const PointParams &P, const Splat &splat)
 {
     constexpr int G = Group<DT>::kPoints;
     constexpr bool kPrefetch = (DT == kF32);
-    const uint32_t full = n / G;
-    const uint32_t groups = groups_of<DT>(n);
+    const uint32_t full = min(n / G, g_end);
     const uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t g = g_begin + blockIdx.x * blockDim.x + threadIdx.x;
     uint4 next[3];
     if (kPrefetch && g < full)
         load_words(src, g, next);
-    while (g < groups) {
+    while (g < g_end) {
         const uint32_t gn = g + stride;
         if (g < full) {
             uint4 q[3];
@@ -45,7 +48,7 @@ __device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t
                 load_words(src, g, q);
             }
             if constexpr (DT == kF32) {
-                process_words<DT, kDisplace, kSplat>(q, g * G, G, P);
+                process_words<DT, kDisplace, kSplat>(q, g * G, G, P, splat);
                 if constexpr (kDisplace)
                     store_words(dst, g, q);
             } else {
@@ -55,7 +58,7 @@ __device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t
                     store_words(dst, g, q);
                 }
                 if constexpr (kSplat)
-                    splat_packed<DT>(q, g * G, P);
+                    splat_packed<DT>(q, g * G, P, splat);
             }
         } else {
             process_tail<DT, kDisplace, kSplat>(src, dst, n, g * G, P);
@@ -76,12 +79,39 @@ __device__ __forceinline__ void enter_dependent_grid()
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Launches a kernel that starts with enter_dependent_grid() with programmatic
+// stream serialization: its CTAs may be scheduled while the kernel before it on
+// the stream finishes, and it waits for that kernel's completion itself.
+// Measured on the 2^22-point 1920x1080 orbit: the resolve after the point
+// kernel 50.3 -> 48.9 us per flushed frame; the next frame's point kernel after
+// the resolve 45.1 -> 43.5 us per back-to-back frame.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s,
+                                    Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // FP32 storage: the compiler's own register choice (48), measured fastest.
-template <bool kDisplace, bool kSplat>
-__global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParams P)
+// Groups g_begin .. g_end - 1; `splat` is the splat policy (mmr_points.cuh,
+// mmr_tiles.cuh).
+template <bool kDisplace, bool kSplat, typename Splat>
+__global__ void points_kernel(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
+                              PointParams P, Splat splat)
 {
     enter_dependent_grid();
-    points_body<kF32, kDisplace, kSplat>(src, dst, n, P);
+    splat.on_entry();
+    points_body<kF32, kDisplace, kSplat>(src, dst, n, g_begin, g_end, P, splat);
 }
 
 // 16-bit storage.  A group holds 8 points, twice the work per load, so the
@@ -93,24 +123,36 @@ __global__ void points_kernel(const void *src, void *dst, uint32_t n, PointParam
 // coordinates kept: binary16 348.4 -> 347.1 us, bfloat16 355.6 -> 351.7 us.
 // A register cap, unlike a launch bound, leaves every block size up to 1024
 // valid.
-template <int DT, bool kDisplace, bool kSplat>
-__global__ void __maxnreg__(kSplat ? 40 : 48) points_kernel_narrow(const void *src, void *dst, uint32_t n, PointParams P)
+template <int DT, bool kDisplace, bool kSplat, typename Splat>
+__global__ void __maxnreg__(kSplat ? 40 : 48) points_kernel_narrow(const void *src, void *dst, uint32_t n,
+                                                                   uint32_t g_begin, uint32_t g_end, PointParams P,
+                                                                   Splat splat)
 {
     enter_dependent_grid();
-    points_body<DT, kDisplace, kSplat>(src, dst, n, P);
+    splat.on_entry();
+    points_body<DT, kDisplace, kSplat>(src, dst, n, g_begin, g_end, P, splat);
 }
 
-// Disc markers: as points_kernel (one thread per 48-byte group), each point
-// splatted as a disc of radius P.disc_r pixels instead of one pixel.
-template <int DT, bool kDisplace>
-__global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, PointParams P)
+// The depth bounds of the tiles the first pass marked (mmr_tiles.cuh).
+__global__ void tile_bound_kernel(const unsigned long long *__restrict__ keys, int W, int H, TileBounds T)
+{
+    enter_dependent_grid();
+    tile_bound_body(keys, W, H, T);
+}
+
+// Disc markers: as points_kernel (one thread per 48-byte group, groups
+// g_begin .. g_end - 1), each point splatted as a disc of radius P.disc_r
+// pixels instead of one pixel.  With kCull, a disc that lies behind the depth
+// bounds of every tile its candidate box touches is skipped (mmr_disc.cuh).
+template <int DT, bool kDisplace, bool kCull>
+__global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
+                                   PointParams P, DiscBounds T)
 {
     enter_dependent_grid();
     constexpr int G = Group<DT>::kPoints;
     const uint32_t full = n / G;
-    const uint32_t groups = groups_of<DT>(n);
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
+    for (uint32_t g = g_begin + blockIdx.x * blockDim.x + threadIdx.x; g < g_end; g += stride) {
         const uint32_t i0 = g * G;
         const uint32_t count = min((uint32_t)G, n - i0);
         uint4 q[3];
@@ -136,8 +178,12 @@ __global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, Point
                     v[3 * j + c] = storage_round<DT>(v[3 * j + c]);
             }
             float sx, sy, cw;
-            if (project_screen(v[3 * j], v[3 * j + 1], v[3 * j + 2], P, sx, sy, cw))
-                splat_disc(sx, sy, ((unsigned long long)__float_as_uint(cw) << 32) | (P.id_base + i0 + j), P);
+            if (project_screen(v[3 * j], v[3 * j + 1], v[3 * j + 2], P, sx, sy, cw)) {
+                const DiscBox box = disc_box(sx, sy, P);
+                if (kCull && disc_behind_bounds(box, __float_as_uint(cw), T))
+                    continue;
+                splat_disc(sx, sy, depth_key(cw, P.id_base + i0 + j), P, box);
+            }
         }
         if constexpr (kDisplace) {
             if (g < full) {
@@ -155,26 +201,52 @@ __global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, Point
     }
 }
 
-template <int DT>
-static cudaError_t launch_disc_dt(const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
-                                  cudaStream_t s)
+// The depth bounds of every 32x32 tile, for the culled disc pass.
+__global__ void disc_tile_bound_kernel(const unsigned long long *__restrict__ keys, int W, int H, DiscBounds T)
 {
-    const uint64_t groups = groups_of<DT>(n);
+    enter_dependent_grid();
+    disc_tile_bound_body(keys, W, H, T);
+}
+
+template <int DT, bool kCull>
+static cudaError_t launch_disc_range(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
+                                     const PointParams &P, bool displace, const DiscBounds &T, cudaStream_t s)
+{
+    const uint64_t groups = g_end - g_begin;
     const int grid = (int)std::max<uint64_t>(1, (groups + 63) / 64);
     if (displace)
-        return launch_dependent(points_disc_kernel<DT, true>, grid, 64, s, src, dst, n, P);
-    return launch_dependent(points_disc_kernel<DT, false>, grid, 64, s, src, dst, n, P);
+        return launch_dependent(points_disc_kernel<DT, true, kCull>, grid, 64, s, src, dst, n, g_begin, g_end, P, T);
+    return launch_dependent(points_disc_kernel<DT, false, kCull>, grid, 64, s, src, dst, n, g_begin, g_end, P, T);
+}
+
+template <int DT>
+static cudaError_t launch_disc_dt(const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
+                                  const DiscBounds *T, int bound_shift, int sm_count, cudaStream_t s)
+{
+    const uint32_t groups = groups_of<DT>(n);
+    if (!T)
+        return launch_disc_range<DT, false>(src, dst, n, 0, groups, P, displace, DiscBounds{}, s);
+    const uint32_t ga = groups >> bound_shift;
+    cudaError_t e = launch_disc_range<DT, false>(src, dst, n, 0, ga, P, displace, *T, s);
+    if (e != cudaSuccess)
+        return e;
+    const uint64_t tiles = (uint64_t)T->tiles_w * T->tiles_h;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((tiles + 7) / 8, (uint64_t)sm_count * 16));
+    e = launch_dependent(disc_tile_bound_kernel, grid, 256, s, (const unsigned long long *)P.keys, P.W, P.H, *T);
+    if (e != cudaSuccess)
+        return e;
+    return launch_disc_range<DT, true>(src, dst, n, ga, groups, P, displace, *T, s);
 }
 
 cudaError_t launch_points_disc(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
-                               bool displace, cudaStream_t s)
+                               bool displace, const DiscBounds *T, int bound_shift, int sm_count, cudaStream_t s)
 {
     if (n == 0)
         return cudaSuccess;
     switch (dtype) {
-    case kF32: return launch_disc_dt<kF32>(src, dst, n, P, displace, s);
-    case kF16: return launch_disc_dt<kF16>(src, dst, n, P, displace, s);
-    case kBF16: return launch_disc_dt<kBF16>(src, dst, n, P, displace, s);
+    case kF32: return launch_disc_dt<kF32>(src, dst, n, P, displace, T, bound_shift, sm_count, s);
+    case kF16: return launch_disc_dt<kF16>(src, dst, n, P, displace, T, bound_shift, sm_count, s);
+    case kBF16: return launch_disc_dt<kBF16>(src, dst, n, P, displace, T, bound_shift, sm_count, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -322,29 +394,6 @@ __global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
 
 // ---------------------------------------------------------------- launchers
 
-// Launches a kernel that starts with enter_dependent_grid() with programmatic
-// stream serialization: its CTAs may be scheduled while the kernel before it on
-// the stream finishes, and it waits for that kernel's completion itself.
-// Measured on the 2^22-point 1920x1080 orbit: the resolve after the point
-// kernel 50.3 -> 48.9 us per flushed frame; the next frame's point kernel after
-// the resolve 45.1 -> 43.5 us per back-to-back frame.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s,
-                                    Args... args)
-{
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 static int grid_for(uint64_t work_items, const LaunchShape &ls)
 {
     if (ls.ctas_per_sm > 0)
@@ -357,24 +406,87 @@ static int grid_for(uint64_t work_items, const LaunchShape &ls)
     return (int)blocks;
 }
 
+template <int DT, typename Splat>
+static cudaError_t launch_points_range(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
+                                       const PointParams &P, bool displace, bool splat_on, const Splat &splat,
+                                       const LaunchShape &ls, cudaStream_t s)
+{
+    const int grid = grid_for(g_end - g_begin, ls);
+    if constexpr (!std::is_same<Splat, SplatDirect>::value) {
+        // the other policies only ever run with displacement and splat, or splat alone
+        if (!splat_on)
+            return cudaErrorInvalidValue;
+    }
+    if constexpr (DT == kF32) {
+        if (displace && splat_on)
+            return launch_dependent(points_kernel<true, true, Splat>, grid, ls.threads, s, src, dst, n, g_begin, g_end,
+                                    P, splat);
+        if constexpr (std::is_same<Splat, SplatDirect>::value) {
+            if (displace)
+                return launch_dependent(points_kernel<true, false, Splat>, grid, ls.threads, s, src, dst, n, g_begin,
+                                        g_end, P, splat);
+        }
+        return launch_dependent(points_kernel<false, true, Splat>, grid, ls.threads, s, src, dst, n, g_begin, g_end,
+                                P, splat);
+    } else {
+        if (displace && splat_on)
+            return launch_dependent(points_kernel_narrow<DT, true, true, Splat>, grid, ls.threads, s, src, dst, n,
+                                    g_begin, g_end, P, splat);
+        if constexpr (std::is_same<Splat, SplatDirect>::value) {
+            if (displace)
+                return launch_dependent(points_kernel_narrow<DT, true, false, Splat>, grid, ls.threads, s, src, dst,
+                                        n, g_begin, g_end, P, splat);
+        }
+        return launch_dependent(points_kernel_narrow<DT, false, true, Splat>, grid, ls.threads, s, src, dst, n,
+                                g_begin, g_end, P, splat);
+    }
+}
+
 template <int DT>
 static cudaError_t launch_points_dt(const void *src, void *dst, uint32_t n, const PointParams &P, bool displace,
                                     bool splat, const LaunchShape &ls, cudaStream_t s)
 {
-    const uint64_t groups = groups_of<DT>(n);
-    const int grid = grid_for(groups, ls);
-    if constexpr (DT == kF32) {
-        if (displace && splat)
-            return launch_dependent(points_kernel<true, true>, grid, ls.threads, s, src, dst, n, P);
-        if (displace)
-            return launch_dependent(points_kernel<true, false>, grid, ls.threads, s, src, dst, n, P);
-        return launch_dependent(points_kernel<false, true>, grid, ls.threads, s, src, dst, n, P);
-    } else {
-        if (displace && splat)
-            return launch_dependent(points_kernel_narrow<DT, true, true>, grid, ls.threads, s, src, dst, n, P);
-        if (displace)
-            return launch_dependent(points_kernel_narrow<DT, true, false>, grid, ls.threads, s, src, dst, n, P);
-        return launch_dependent(points_kernel_narrow<DT, false, true>, grid, ls.threads, s, src, dst, n, P);
+    const uint32_t groups = groups_of<DT>(n);
+    if (splat && ls.kernel == kKernelWarpAgg)
+        return launch_points_range<DT>(src, dst, n, 0, groups, P, displace, true, SplatWarpAggregated{}, ls, s);
+    return launch_points_range<DT>(src, dst, n, 0, groups, P, displace, splat, SplatDirect{}, ls, s);
+}
+
+// Depth-bounded frame: the first groups_a groups with the marking splat, the
+// bound kernel over the marked tiles, then the remaining groups with the
+// bounded splat.
+template <int DT>
+static cudaError_t launch_points_bounded_dt(const void *src, void *dst, uint32_t n, const PointParams &P,
+                                            bool displace, const TileBounds &T, uint32_t tiles,
+                                            const LaunchShape &ls, cudaStream_t s)
+{
+    const uint32_t groups = groups_of<DT>(n);
+    const uint32_t ga = groups >> ls.bound_shift;
+    cudaError_t e = launch_points_range<DT>(src, dst, n, 0, ga, P, displace, true, SplatMarkTiles{T}, ls, s);
+    if (e != cudaSuccess)
+        return e;
+    // one warp per marked tile: the grid covers every tile in the worst case, capped at 16 CTAs per SM
+    const int warps_per_cta = 8;
+    const uint64_t need = ((uint64_t)tiles + warps_per_cta - 1) / warps_per_cta;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)ls.sm_count * 16));
+    e = launch_dependent(tile_bound_kernel, grid, 32 * warps_per_cta, s, (const unsigned long long *)P.keys, P.W, P.H,
+                         T);
+    if (e != cudaSuccess)
+        return e;
+    return launch_points_range<DT>(src, dst, n, ga, groups, P, displace, true, SplatBelowTileBound{T}, ls, s);
+}
+
+cudaError_t launch_points_bounded(int dtype, const void *src, void *dst, uint32_t n, const PointParams &P,
+                                  bool displace, const TileBounds &T, uint32_t tiles, const LaunchShape &ls,
+                                  cudaStream_t s)
+{
+    if (n == 0)
+        return cudaSuccess;
+    switch (dtype) {
+    case kF32: return launch_points_bounded_dt<kF32>(src, dst, n, P, displace, T, tiles, ls, s);
+    case kF16: return launch_points_bounded_dt<kF16>(src, dst, n, P, displace, T, tiles, ls, s);
+    case kBF16: return launch_points_bounded_dt<kBF16>(src, dst, n, P, displace, T, tiles, ls, s);
+    default: return cudaErrorInvalidValue;
     }
 }
 

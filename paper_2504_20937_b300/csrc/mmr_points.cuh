@@ -28,6 +28,41 @@ struct Group<kBF16> {
     static constexpr int kPoints = 8;
 };
 
+// How a projected point reaches the depth-id buffer.  A point kernel body
+// calls its splat policy for every point that projected into the frame, with
+// the pixel's column and row and the key; a policy whose kWarpWide is true is
+// called for every point, with ok = whether it projected (all lanes of a warp
+// call it together, which warp-level policies rely on).  A kernel calls
+// on_entry() once per thread before its first point.  The default policy is
+// the depth-tested splat of mmr_device.cuh.
+struct SplatDirect {
+    static constexpr bool kWarpWide = false;
+
+    __device__ __forceinline__ void on_entry() const {}
+
+    __device__ __forceinline__ void operator()(const PointParams &P, bool, uint32_t ix, uint32_t iy,
+                                               unsigned long long key) const
+    {
+        splat_key(P.keys, iy * (uint32_t)P.W + ix, key);
+    }
+};
+
+// One projected point through a splat policy (see above).
+template <typename Splat>
+__device__ __forceinline__ void splat_point(const Splat &splat, const PointParams &P, bool in_range, float x,
+                                            float y, float z, uint32_t id)
+{
+    uint32_t ix = 0, iy = 0;
+    float cw = 0.0f;
+    if constexpr (Splat::kWarpWide) {
+        const bool ok = in_range && project_pixel(x, y, z, P, ix, iy, cw);
+        splat(P, ok, ix, iy, depth_key(cw, id));
+    } else {
+        if (in_range && project_pixel(x, y, z, P, ix, iy, cw))
+            splat(P, true, ix, iy, depth_key(cw, id));
+    }
+}
+
 template <int DT>
 __device__ __forceinline__ float load_coord(const void *pos, uint64_t k)
 {
@@ -60,7 +95,8 @@ __device__ __forceinline__ float storage_round(float f)
 
 // The ragged tail: points i0 .. n-1 of the last, partial group, with scalar
 // accesses (the vector path would read past n).  Reads src, writes dst
-// (the same buffer for an in-place step).
+// (the same buffer for an in-place step).  One thread does this, so it
+// always takes the direct splat.
 template <int DT, bool kDisplace, bool kSplat>
 __device__ __forceinline__ void process_tail(const void *src, void *dst, uint32_t n, uint32_t i0,
                                              const PointParams &P)
@@ -145,23 +181,21 @@ __device__ __forceinline__ void displace_packed(uint4 (&q)[3], uint32_t i0, cons
     }
 }
 
-template <int DT>
-__device__ __forceinline__ void splat_packed(const uint4 (&q)[3], uint32_t i0, const PointParams &P)
+template <int DT, typename Splat = SplatDirect>
+__device__ __forceinline__ void splat_packed(const uint4 (&q)[3], uint32_t i0, const PointParams &P,
+                                             const Splat &splat = Splat{})
 {
     static_assert(DT != kF32, "16-bit groups only");
     constexpr int G = Group<DT>::kPoints;
 #pragma unroll
-    for (int j = 0; j < G; ++j) {
-        uint32_t px;
-        unsigned long long key;
-        if (project_key(word_coord<DT>(q, 3 * j), word_coord<DT>(q, 3 * j + 1), word_coord<DT>(q, 3 * j + 2),
-                        P.id_base + i0 + j, P, px, key))
-            splat_key(P.keys, px, key);
-    }
+    for (int j = 0; j < G; ++j)
+        splat_point(splat, P, true, word_coord<DT>(q, 3 * j), word_coord<DT>(q, 3 * j + 1),
+                    word_coord<DT>(q, 3 * j + 2), P.id_base + i0 + j);
 }
 
-template <int DT, bool kDisplace, bool kSplat>
-__device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32_t count, const PointParams &P)
+template <int DT, bool kDisplace, bool kSplat, typename Splat = SplatDirect>
+__device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32_t count, const PointParams &P,
+                                              const Splat &splat = Splat{})
 {
     constexpr int G = Group<DT>::kPoints;
     float v[3 * G];
@@ -183,13 +217,8 @@ __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32
     }
     if constexpr (kSplat) {
 #pragma unroll
-        for (int j = 0; j < G; ++j) {
-            uint32_t px;
-            unsigned long long key;
-            if ((uint32_t)j < count &&
-                project_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], P.id_base + i0 + j, P, px, key))
-                splat_key(P.keys, px, key);
-        }
+        for (int j = 0; j < G; ++j)
+            splat_point(splat, P, (uint32_t)j < count, v[3 * j], v[3 * j + 1], v[3 * j + 2], P.id_base + i0 + j);
     }
 }
 

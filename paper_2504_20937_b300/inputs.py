@@ -165,13 +165,15 @@ class ViewerRequest:
     init_seed: int
 
 
-def serving_trace(requests: int = 10_000, seed: int = 5, rate_hz: float = 400.0,
-                  frames_per_viewer: int = 16, private_lo: float = 1e4, private_hi: float = 1e6,
+def serving_trace(requests: int = 10_000, seed: int = 5, rate_hz: float = 40.0,
+                  frames_per_viewer: int = 50, private_lo: float = 1e4, private_hi: float = 1e6,
                   resolutions=((640, 480), (1920, 1080), (3840, 2160))) -> list[ViewerRequest]:
     """Poisson arrivals of viewers; each viewer asks for `frames_per_viewer`
-    frames of its own resolution, with its own private cloud.  At the default
-    rate the number of viewers on the engine moves between roughly 8 and the
-    64-viewer cap."""
+    frames of its own resolution, with its own private cloud.  Served at a
+    60 Hz display rate (one frame per viewer per refresh), a viewer stays
+    frames_per_viewer / 60 s, so on average rate_hz * frames_per_viewer / 60
+    viewers share the engine: about 33 at the defaults, with Poisson spread
+    (a standard deviation near 6) inside the 8-64 range."""
     rng = np.random.Generator(np.random.PCG64(seed))
     viewers = max(1, requests // frames_per_viewer)
     t = 0.0

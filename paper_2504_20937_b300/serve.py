@@ -6,9 +6,18 @@ loop admits arrived viewers while there is a free slot and the engine's
 device-memory budget allows (a refused viewer waits in FIFO order), runs one
 engine tick per iteration (one frame for every active viewer, all of them
 batched into the same kernels), and retires viewers when their last frame is
-done, which frees memory for the queue.  A frame's latency is the time from
-its request (the viewer's arrival for its first frame, the completion of its
-previous frame otherwise) to the completion of the tick that rendered it.
+done, which frees memory for the queue.
+
+Two pacings.  With a display rate (tick_hz > 0, the default 60 Hz) every
+active viewer asks for a frame at each display refresh, as a viewer whose
+display shows one frame per refresh would: ticks start on the refresh grid,
+a frame's latency runs from its refresh (from the viewer's arrival for its
+first frame) to the completion of the tick that rendered it, and a refresh
+that comes while a tick is still running is dropped (counted).  The number
+of viewers on the engine is then set by the arrivals and the session length,
+not by the engine's speed, so two engines see the same load.  With
+tick_hz = 0 ticks run back to back, a frame's request being the completion
+of the viewer's previous frame: the engine's saturation throughput.
 
 The scheduling decisions and the bookkeeping live here; all device work is
 in the library.
@@ -42,6 +51,7 @@ class ServeConfig:
     fovy_deg: float = 60.0
     znear: float = 0.1
     zfar: float = 100.0
+    tick_hz: float = 60.0           # display refresh rate; 0 = ticks back to back
 
 
 @dataclass
@@ -57,11 +67,22 @@ class ServeStats:
     max_active: int = 0
     refused_for_budget: int = 0
     queue_wait_ms: list = field(default_factory=list)
+    tick_start_s: list = field(default_factory=list)
+    tick_hz: float = 0.0
+    refreshes_dropped: int = 0
+    steady_window_s: tuple = (0.0, 0.0)   # ticks starting in it count for the steady-state concurrency
 
     def summary(self) -> dict:
         lat = np.asarray(self.latencies_ms) if self.latencies_ms else np.zeros(1)
         steady = np.asarray(self.steady_latencies_ms) if self.steady_latencies_ms else np.zeros(1)
-        return {"frames": self.frames, "ticks": self.ticks, "wall_s": self.wall_s,
+        t = np.asarray(self.tick_start_s)
+        act = np.asarray(self.active_per_tick)
+        win = (t >= self.steady_window_s[0]) & (t <= self.steady_window_s[1]) if t.size else t.astype(bool)
+        return {"tick_hz": self.tick_hz, "frames": self.frames, "ticks": self.ticks, "wall_s": self.wall_s,
+                "refreshes_dropped": self.refreshes_dropped,
+                "steady_window_s": list(self.steady_window_s),
+                "mean_active_viewers_steady": float(act[win].mean()) if win.any() else 0.0,
+                "min_active_viewers_steady": int(act[win].min()) if win.any() else 0,
                 "frames_per_s": self.frames / self.wall_s if self.wall_s else 0.0,
                 "points_per_s": self.points_rendered / self.wall_s if self.wall_s else 0.0,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -130,13 +151,19 @@ class ContinuousBatcher:
         """(engine id, request, frame index) of every frame the next tick renders."""
         return [(vid, st[0], st[1]) for vid, st in self.active.items()]
 
-    def tick_done(self, done: float):
+    def tick_done(self, done: float, refresh: float | None = None):
         """Account one tick finished at time `done`; returns (latencies of
-        first frames, latencies of later frames, retired engine ids)."""
+        first frames, latencies of later frames, retired engine ids).  A
+        first frame's latency runs from the viewer's arrival; a later frame's
+        from `refresh`, the display refresh that asked for it, or without a
+        display rate from the completion of the viewer's previous frame."""
         first, later, finished = [], [], []
         for vid, st in self.active.items():
             req, k, req_time = st
-            (first if k == 0 else later).append(done - req_time)
+            if k == 0:
+                first.append(done - req_time)
+            else:
+                later.append(done - (refresh if refresh is not None else req_time))
             st[1], st[2] = k + 1, done
             if st[1] >= req.frames:
                 finished.append(vid)
@@ -155,17 +182,23 @@ def run_trace(trace, cfg: ServeConfig, roundtrip: bool = False, clouds=None, sha
     """Serve every request of `trace`; returns the statistics.
 
     clouds: optional {viewer: stored private cloud} (generated if missing);
-    shared: optional stored shared cloud (generated if missing).
+    shared: optional stored shared cloud (generated if missing).  Pacing by
+    cfg.tick_hz (see the module docstring).
     """
     if shared is None:
         shared = inputs.encode(inputs.uniform_cloud(cfg.shared_n, cfg.shared_seed), cfg.dtype)
     if clouds is None:
         clouds = {r.viewer: private_cloud(r, cfg.dtype) for r in trace}
     host_clouds = {v: _to_torch(c).pin_memory() for v, c in clouds.items()}
-    stats = ServeStats()
+    stats = ServeStats(tick_hz=cfg.tick_hz)
+    if trace:
+        # steady state: after the first viewer's session could have filled up, until the last arrival
+        ramp = max(r.frames for r in trace) / cfg.tick_hz if cfg.tick_hz > 0 else 0.0
+        stats.steady_window_s = (min(r.arrival_s for r in trace) + ramp, max(r.arrival_s for r in trace))
     stream = torch.cuda.current_stream()
     sched = ContinuousBatcher(cfg.max_viewers)
     sched.load(trace)
+    period = 1.0 / cfg.tick_hz if cfg.tick_hz > 0 else 0.0
     with Server(cfg.shared_n, cfg.dtype, cfg.shared_seed, 0, cfg.amplitude, cfg.budget_bytes) as srv:
         srv.shared_points().copy_(_to_torch(shared))
         srv.set_shared_color(cfg.shared_color)
@@ -176,34 +209,52 @@ def run_trace(trace, cfg: ServeConfig, roundtrip: bool = False, clouds=None, sha
             return srv.try_add_viewer(req.private_n, req.W, req.H, seed=req.init_seed, cloud=1 + req.viewer,
                                       amplitude=cfg.amplitude, color=0xFF000000 | (req.viewer & 0xFFFFFF))
 
+        refresh_k = 0
         t0 = time.perf_counter()
         while sched.busy():
             now = time.perf_counter() - t0
-            sched.arrive(now)
+            refresh = None
+            if period:
+                refresh = refresh_k * period
+                if now < refresh:
+                    time.sleep(refresh - now)
+                    now = time.perf_counter() - t0
+                sched.arrive(refresh)
+            else:
+                sched.arrive(now)
             for vid, req in sched.admit(try_add):
                 srv.viewer_points(vid).copy_(host_clouds[req.viewer], non_blocking=True)
                 stats.queue_wait_ms.append(1e3 * max(0.0, (time.perf_counter() - t0) - req.arrival_s))
             due = sched.frames_due()
             if not due:
-                nxt = sched.next_arrival()
-                if nxt is not None:
-                    time.sleep(max(0.0, min(nxt - now, 0.001)))
+                if period:
+                    refresh_k += 1
+                else:
+                    nxt = sched.next_arrival()
+                    if nxt is not None:
+                        time.sleep(max(0.0, min(nxt - now, 0.001)))
                 continue
             stats.max_active = max(stats.max_active, len(due))
             stats.active_per_tick.append(len(due))
+            stats.tick_start_s.append(refresh if period else now)
             for vid, req, k in due:
                 srv.set_camera(vid, viewer_eye(req, k, cfg), CENTRE, UP, cfg.fovy_deg, cfg.znear, cfg.zfar)
             srv.tick(stream, roundtrip=roundtrip)
             stats.tick_ms.append(srv.last_tick_ms())      # waits for the tick
             done = time.perf_counter() - t0
             stats.ticks += 1
-            first, later, finished = sched.tick_done(done)
+            first, later, finished = sched.tick_done(done, refresh)
             stats.latencies_ms += [1e3 * x for x in first + later]
             stats.steady_latencies_ms += [1e3 * x for x in later]
             stats.frames += len(due)
             stats.points_rendered += sum(cfg.shared_n + req.private_n for _, req, _ in due)
             for vid in finished:
                 srv.remove_viewer(vid)
+            if period:
+                # the next refresh after this tick; the ones it ran over are dropped
+                nxt = max(refresh_k + 1, int(np.ceil(done / period)))
+                stats.refreshes_dropped += nxt - refresh_k - 1
+                refresh_k = nxt
         stats.refused_for_budget = sched.refused
         stats.wall_s = time.perf_counter() - t0
     return stats

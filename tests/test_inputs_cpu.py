@@ -83,14 +83,21 @@ def test_batched_table_recipe():
 
 
 def test_serving_trace_recipe():
-    """10,000 frame requests as 625 viewers of 16 frames, Poisson arrivals at
-    400 viewers/s, private clouds log-uniform in [1e4, 1e6), three resolutions."""
+    """10,000 frame requests as 200 viewers of 50 frames, Poisson arrivals at
+    40 viewers/s, private clouds log-uniform in [1e4, 1e6), three resolutions.
+    At 60 frames a second per viewer the concurrency (viewers whose 50/60 s
+    session covers a moment) stays inside 8..64 once the first sessions have
+    filled up, until the last arrival."""
     tr = inputs.serving_trace()
-    assert len(tr) == 625 and sum(r.frames for r in tr) == 10_000
+    assert len(tr) == 200 and sum(r.frames for r in tr) == 10_000
     arr = np.array([r.arrival_s for r in tr])
     assert np.all(np.diff(arr) > 0)
     gaps = np.diff(np.concatenate([[0.0], arr]))
-    assert abs(gaps.mean() - 1 / 400) < 5 * (1 / 400) / math.sqrt(len(gaps))
+    assert abs(gaps.mean() - 1 / 40) < 5 * (1 / 40) / math.sqrt(len(gaps))
+    session = 50 / 60.0
+    grid = np.arange(arr[0] + session, arr[-1], 1 / 60.0)
+    conc = np.array([np.count_nonzero((arr <= t) & (arr + session > t)) for t in grid])
+    assert 8 <= conc.min() and conc.max() <= 64 and 25 <= conc.mean() <= 42
     pn = np.array([r.private_n for r in tr])
     assert pn.min() >= 10_000 and pn.max() < 1_000_000
     assert {(r.W, r.H) for r in tr} == {(640, 480), (1920, 1080), (3840, 2160)}

@@ -358,9 +358,10 @@ def test_checkpoint_and_resume_is_bit_exact():
         assert np.array_equal(ctx.frame_rgba().cpu().numpy(), want_rgba)
 
 
+@pytest.mark.parametrize("kernel", ["grid", "depth_bound"])
 @pytest.mark.parametrize("radius", [0.5, 1.0, 1.5, 2.0, 3.0, 64.0])
 @pytest.mark.parametrize("W,H", [(64, 64), (61, 37)])
-def test_disc_markers_at_exact_pixel_distances(radius, W, H):
+def test_disc_markers_at_exact_pixel_distances(radius, W, H, kernel):
     """Disc centres exactly on pixel centres and pixel edges and one ulp or
     2^-20 either side of them, so many candidate pixels sit exactly at, or a
     rounding away from, distance r; discs partly off the frame.  With the
@@ -385,6 +386,7 @@ def test_disc_markers_at_exact_pixel_distances(radius, W, H):
         ctx.alloc_points(len(pos), "f32").copy_(torch.from_numpy(pos))
         ctx.set_matrix(M, 0.5, 2.0)
         ctx.set_marker(radius)
+        ctx.set_launch(64, 0, kernel)
         ctx.render()
         torch.cuda.synchronize()
         gkeys = ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64)

@@ -161,17 +161,31 @@ def test_serve_budget_admission_and_release():
 def test_serve_request_loop_small_trace():
     trace = inputs.serving_trace(requests=200, seed=11, rate_hz=5000.0, frames_per_viewer=5,
                                  private_lo=1e3, private_hi=2e4, resolutions=((64, 48), (160, 90), (320, 240)))
-    cfg = ServeConfig(shared_n=50_000, max_viewers=8)
+    cfg = ServeConfig(shared_n=50_000, max_viewers=8, tick_hz=0.0)
     stats = run_trace(trace, cfg)
     s = stats.summary()
     assert s["frames"] == sum(r.frames for r in trace)
     assert 0 < s["p50_ms"] <= s["p99_ms"]
     assert 1 <= s["max_active_viewers"] <= 8
     # a budget for the shared cloud plus two of the largest viewers forces queueing on memory
-    tight = ServeConfig(shared_n=50_000, max_viewers=8,
+    tight = ServeConfig(shared_n=50_000, max_viewers=8, tick_hz=0.0,
                         budget_bytes=(50_000 * 12 + 47) // 48 * 48 + 2 * (20_000 * 12 + 48 + 320 * 240 * 20))
     s2 = run_trace(trace, tight).summary()
     assert s2["frames"] == s["frames"] and s2["refused_for_budget"] > 0
+
+
+def test_serve_request_loop_paced_by_a_display_rate():
+    """At 200 Hz refreshes, every frame of every viewer is rendered, each
+    viewer's frames on consecutive ticks, and a later frame's latency (from
+    its refresh) stays below a refresh period when no refresh is dropped."""
+    trace = inputs.serving_trace(requests=300, seed=12, rate_hz=100.0, frames_per_viewer=10,
+                                 private_lo=1e3, private_hi=2e4, resolutions=((64, 48), (160, 90)))
+    cfg = ServeConfig(shared_n=50_000, max_viewers=16, tick_hz=200.0)
+    s = run_trace(trace, cfg).summary()
+    assert s["frames"] == 300 and s["tick_hz"] == 200.0
+    assert s["ticks"] >= 300 // 16
+    if s["refreshes_dropped"] == 0:
+        assert s["p99_ms_after_first"] < 5.0
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])

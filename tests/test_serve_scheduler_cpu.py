@@ -69,3 +69,17 @@ def test_latency_of_first_and_later_frames():
     first, later, done = b.tick_done(1.5)
     assert first == [] and later == [0.5] and done == [0]    # from the previous frame
     assert not b.busy()
+
+
+def test_latency_from_the_display_refresh():
+    """With a display rate a later frame's latency runs from the refresh that
+    asked for it; the first frame's still from the arrival."""
+    b = ContinuousBatcher(max_viewers=4)
+    b.load([_req(0, 0.25, frames=3)])
+    eng = FakeEngine(budget=10**9)
+    b.arrive(0.5)
+    b.admit(eng.try_add)
+    first, later, _ = b.tick_done(0.625, refresh=0.5)
+    assert first == [0.375] and later == []
+    first, later, _ = b.tick_done(1.125, refresh=1.0)       # rendered 1/8 s after its refresh
+    assert first == [] and later == [0.125]
