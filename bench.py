@@ -66,6 +66,12 @@ def parse():
     ap.add_argument("--points", type=int, default=0, help="override the point count (profiling cases)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="position storage of the main timed region (16-bit: profiling cases, with --no-extra)")
+    ap.add_argument("--marker", type=float, default=0.0,
+                    help="disc marker radius in pixels for the main timed region (profiling cases, with --no-extra)")
+    ap.add_argument("--serve-viewers", type=int, default=0,
+                    help="with --leg served: that many viewers of --serve-resolution on the engine for --steps "
+                         "ticks back to back, instead of the trace (profiling cases)")
+    ap.add_argument("--serve-resolution", default="1920x1080", help="WxH of the --serve-viewers viewers")
     ap.add_argument("--leg", default="all", choices=["all", "batched", "served"],
                     help="run one leg alone (profiling cases): batched = the 256-cloud batch for --steps frames, "
                          "served = the zero-copy serving trace of --serve-requests requests")
@@ -258,6 +264,8 @@ def run_ours(args, rank, world, local):
         view.copy_(torch.from_numpy(data if dtype == "f32" else data.view(np.int16)))
         ctx.set_sim(scene.philox_seed, 0, scene.amplitude, 0)
         ctx.set_style(scene.color, scene.background)
+        if args.marker:
+            ctx.set_marker(args.marker)
         if args.launch:
             t, c, k = args.launch.split(",")
             ctx.set_launch(int(t), int(c), int(k) if k.isdigit() else k)
@@ -792,6 +800,38 @@ def run_served(requests=10_000, roundtrip=True):
     return out
 
 
+def run_served_fixed(viewers, W, H, ticks, warm):
+    """`viewers` viewers of W x H (private clouds of 10^5 points) on the
+    serving engine with the 2^24-point shared cloud, `ticks` ticks back to
+    back after `warm` untimed ones: a small, steady case for profilers."""
+    import torch
+    from paper_2504_20937_b300 import serve
+    from paper_2504_20937_b300.api import Server
+    cfg = serve.ServeConfig()
+    shared = inputs.encode(inputs.uniform_cloud(cfg.shared_n, cfg.shared_seed), cfg.dtype)
+    stream = torch.cuda.current_stream()
+    with Server(cfg.shared_n, cfg.dtype, cfg.shared_seed, 0, cfg.amplitude, cfg.budget_bytes) as srv:
+        srv.shared_points().copy_(torch.from_numpy(shared))
+        vids = []
+        for v in range(viewers):
+            vid = srv.add_viewer(100_000, W, H, seed=100 + v, cloud=1 + v, amplitude=cfg.amplitude)
+            srv.viewer_points(vid).copy_(torch.from_numpy(inputs.encode(inputs.uniform_cloud(100_000, 100 + v),
+                                                                         cfg.dtype)))
+            vids.append(vid)
+        srv.set_timing(True)
+        ms = []
+        for t in range(warm + ticks):
+            for k, vid in enumerate(vids):
+                srv.set_camera(vid, inputs.orbit_eye(t, 0.36, 2.0, CENTRE, 0.0, 360.0 * k / viewers), CENTRE, UP,
+                               cfg.fovy_deg, cfg.znear, cfg.zfar)
+            srv.tick(stream)
+            tick_ms = srv.last_tick_ms()
+            if t >= warm:
+                ms.append(tick_ms)
+    return {"viewers": viewers, "resolution": f"{W}x{H}", "ticks": ticks, "mean_tick_ms": statistics.mean(ms),
+            "frames_per_s": viewers / (statistics.mean(ms) / 1e3)}
+
+
 # ---------------------------------------------------------------- reference
 
 def cpu_oracle_rate(sc, stored, frames, points):
@@ -853,8 +893,8 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
-    if args.storage != "f32" and not args.no_extra:
-        raise SystemExit("--storage f16/bf16 times the main region only: add --no-extra")
+    if (args.storage != "f32" or args.marker) and not args.no_extra:
+        raise SystemExit("--storage f16/bf16 and --marker time the main region only: add --no-extra")
     rank, world, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
@@ -866,6 +906,9 @@ def main():
         hbm_gbs, _ = measured_peaks()
         if args.leg == "batched":
             res = run_batched(hbm_gbs, frames=args.steps)
+        elif args.serve_viewers:
+            W, H = (int(v) for v in args.serve_resolution.split("x"))
+            res = run_served_fixed(args.serve_viewers, W, H, args.steps, args.warmup)
         else:
             res = run_served(args.serve_requests, roundtrip=False)
         print(json.dumps({"leg": args.leg, args.leg: res}), flush=True)

@@ -180,16 +180,17 @@ MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t backgrou
  *    each marked tile's keys; the rest of the points skip the depth-buffer
  *    read when they lie behind their tile's bound (they could not win any of
  *    its pixels).  Three point-phase launches; 16 bytes per tile of device
- *    memory, allocated at the first such frame.
+ *    memory, allocated at the first such frame.  mmr_set_depth_bound_split
+ *    sets the first pass's share of the points to 2^-shift (1..10, default
+ *    3: one eighth), for 1-px points and disc markers alike.
  *  kernel = MMR_KERNEL_WARP_AGG: the grid-stride kernel whose lanes that hit
  *    the same pixel in one step elect their nearest point, which alone reads
  *    the key and takes the atomic.
- *  kernel = MMR_KERNEL_AUTO (the default): MMR_KERNEL_DEPTH_BOUND when the
- *    cloud has at least 2^20 points and four points per pixel, else
- *    MMR_KERNEL_GRID (64 threads, one thread per group).
+ *  kernel = MMR_KERNEL_AUTO (the default): MMR_KERNEL_GRID (64 threads, one
+ *    thread per group) for 1-px points.
  * Disc markers (mmr_set_marker) use their own grid-stride kernel (64
  * threads).  Under MMR_KERNEL_DEPTH_BOUND, or MMR_KERNEL_AUTO with at least
- * 2^20 points and 16 discs over each pixel on average (n pi r^2 >= 16 w h),
+ * 2^20 points and 256 discs over each pixel on average (n pi r^2 >= 256 w h),
  * it runs in two passes with depth bounds of 32x32-pixel tiles between them:
  * a later disc behind the bounds of every tile it touches is skipped.
  * Results never depend on the shape or the kernel; only speed does. */
@@ -201,6 +202,7 @@ enum mmr_kernel {
     MMR_KERNEL_AUTO = 4
 };
 MMR_API mmr_status mmr_set_launch(mmr_ctx *ctx, int threads, int ctas_per_sm, int kernel);
+MMR_API mmr_status mmr_set_depth_bound_split(mmr_ctx *ctx, int first_pass_shift);
 
 /* ---- frames ---------------------------------------------------------------- */
 

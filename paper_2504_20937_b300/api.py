@@ -208,6 +208,10 @@ class Context:
         self._check(self._lib.mmr_last_kernel_ms(self._h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
+    def set_depth_bound_split(self, first_pass_shift: int = 3):
+        """Depth-bound kernels: the first pass takes 2^-shift of the points."""
+        self._check(self._lib.mmr_set_depth_bound_split(self._h, first_pass_shift))
+
     def last_frame_kernels(self) -> int:
         """Kernels the latest frame launched (point phase and resolve)."""
         k = C.c_int()

@@ -190,11 +190,13 @@ bool uses_tma(const mmr::LaunchShape &ls) { return ls.kernel == MMR_KERNEL_TMA; 
 
 uint64_t tile_bytes(uint64_t tiles) { return 16 * tiles + 16; }
 
-// The depth-bound paths pay where many points share each pixel: for 1-px
-// points at least four points per pixel on average, for disc markers at
-// least kDiscCoverMin discs over each pixel (n pi r^2 / pixels), and a cloud
-// of at least 2^20 points (smaller clouds are launch-bound).
-constexpr double kDiscCoverMin = 16.0;
+// The depth-bound path pays for disc markers where many discs cover each
+// pixel: at least kDiscCoverMin on average (n pi r^2 / pixels, measured on the
+// 2^22-point 1080p orbit: r = 16, 1600 discs per pixel, 5.86 -> 2.05 ms; r = 4,
+// 100 per pixel, 0.42 -> 0.45 ms), for clouds of at least 2^20 points.  For
+// 1-px points it is chosen only explicitly: on the 64M-point 16-cluster 4K
+// frame it saved 1% in FP32 and cost 9-11% in 16-bit storage.
+constexpr double kDiscCoverMin = 256.0;
 
 bool uses_depth_bound(const mmr_ctx *c)
 {
@@ -204,7 +206,7 @@ bool uses_depth_bound(const mmr_ctx *c)
         return false;
     if (c->disc_r > 0.0f)
         return (double)c->n * 3.14159265358979 * c->disc_r * c->disc_r >= kDiscCoverMin * (double)frame_px(c);
-    return c->n >= 4 * frame_px(c);
+    return false;     // 1-px points: the direct splat (see the measurements in the design notes)
 }
 
 // The tile arrays of the depth-bound path, allocated (zero-filled: no tile
@@ -895,6 +897,16 @@ mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **d
         *rgba = ctx->rgba;
     if (depth_id)
         *depth_id = reinterpret_cast<const uint64_t *>(ctx->keys[ctx->latest_buf]);
+    return MMR_OK;
+}
+
+mmr_status mmr_set_depth_bound_split(mmr_ctx *ctx, int first_pass_shift)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (first_pass_shift < 1 || first_pass_shift > 10)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_depth_bound_split: shift %d outside 1..10", first_pass_shift);
+    ctx->launch.bound_shift = first_pass_shift;
     return MMR_OK;
 }
 

@@ -48,7 +48,7 @@ __device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t
                 load_words(src, g, q);
             }
             if constexpr (DT == kF32) {
-                process_words<DT, kDisplace, kSplat>(q, g * G, G, P, splat);
+                process_words<DT, kDisplace, kSplat, Splat, true>(q, g * G, G, P, splat);
                 if constexpr (kDisplace)
                     store_words(dst, g, q);
             } else {
@@ -102,11 +102,16 @@ static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int thre
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-// FP32 storage: the compiler's own register choice (48), measured fastest.
+// FP32 storage.  Points are projected two at a time on packed FP32 pairs
+// (project_pixel2): 62 registers uncapped; under a cap of 60 the compiler
+// finds 55 without spilling (at 56 it spills 8 bytes).  Measured on the
+// 64M-point 16-cluster 4K frame against the one-point projection at 47
+// registers, on one box: 444.5 -> 408.9 us (cap 56: 408.0 us with the spill,
+// cap 64: 414.3 us); the 2^22-point 1080p frame 43.8 -> 42.9 us.
 // Groups g_begin .. g_end - 1; `splat` is the splat policy (mmr_points.cuh,
 // mmr_tiles.cuh).
 template <bool kDisplace, bool kSplat, typename Splat>
-__global__ void points_kernel(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
+__global__ void __maxnreg__(60) points_kernel(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
                               PointParams P, Splat splat)
 {
     enter_dependent_grid();

@@ -63,6 +63,30 @@ __device__ __forceinline__ void splat_point(const Splat &splat, const PointParam
     }
 }
 
+// Two points through a splat policy, projected together (project_pixel2);
+// the same calls, in the same order, as splat_point on each.
+template <typename Splat>
+__device__ __forceinline__ void splat_pair(const Splat &splat, const PointParams &P, bool in_a, float xa, float ya,
+                                           float za, uint32_t ida, bool in_b, float xb, float yb, float zb,
+                                           uint32_t idb)
+{
+    bool oka, okb;
+    uint32_t ixa, iya, ixb, iyb;
+    float cwa, cwb;
+    project_pixel2(xa, ya, za, xb, yb, zb, P, oka, ixa, iya, cwa, okb, ixb, iyb, cwb);
+    oka = oka && in_a;
+    okb = okb && in_b;
+    if constexpr (Splat::kWarpWide) {
+        splat(P, oka, ixa, iya, depth_key(cwa, ida));
+        splat(P, okb, ixb, iyb, depth_key(cwb, idb));
+    } else {
+        if (oka)
+            splat(P, true, ixa, iya, depth_key(cwa, ida));
+        if (okb)
+            splat(P, true, ixb, iyb, depth_key(cwb, idb));
+    }
+}
+
 template <int DT>
 __device__ __forceinline__ float load_coord(const void *pos, uint64_t k)
 {
@@ -193,7 +217,9 @@ __device__ __forceinline__ void splat_packed(const uint4 (&q)[3], uint32_t i0, c
                     word_coord<DT>(q, 3 * j + 2), P.id_base + i0 + j);
 }
 
-template <int DT, bool kDisplace, bool kSplat, typename Splat = SplatDirect>
+// kPairs: project the points two at a time on packed FP32 pairs
+// (project_pixel2): fewer instructions, more registers.
+template <int DT, bool kDisplace, bool kSplat, typename Splat = SplatDirect, bool kPairs = false>
 __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32_t count, const PointParams &P,
                                               const Splat &splat = Splat{})
 {
@@ -216,9 +242,18 @@ __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32
         }
     }
     if constexpr (kSplat) {
+        if constexpr (kPairs) {
 #pragma unroll
-        for (int j = 0; j < G; ++j)
-            splat_point(splat, P, (uint32_t)j < count, v[3 * j], v[3 * j + 1], v[3 * j + 2], P.id_base + i0 + j);
+            for (int j = 0; j < G; j += 2)
+                splat_pair(splat, P, (uint32_t)j < count, v[3 * j], v[3 * j + 1], v[3 * j + 2], P.id_base + i0 + j,
+                           (uint32_t)j + 1 < count, v[3 * j + 3], v[3 * j + 4], v[3 * j + 5],
+                           P.id_base + i0 + j + 1);
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                splat_point(splat, P, (uint32_t)j < count, v[3 * j], v[3 * j + 1], v[3 * j + 2],
+                            P.id_base + i0 + j);
+        }
     }
 }
 

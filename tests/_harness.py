@@ -35,7 +35,7 @@ def download_frame(ctx):
 
 def gpu_run(stored, dtype, W, H, seed, amplitude, frames, eye_fn, fovy=60.0, znear=0.1, zfar=100.0,
             cloud=0, first_step=0, launch=None, colors=None, color=0xFFFFFFFF, background=0,
-            mode="fused", keep_every=None):
+            mode="fused", keep_every=None, bound_shift=None):
     """Run `frames` frames on the GPU; returns (positions, keys, rgba) of the
     last frame, plus the per-frame (keys, rgba) of the frames in keep_every."""
     from paper_2504_20937_b300.api import Context
@@ -49,6 +49,8 @@ def gpu_run(stored, dtype, W, H, seed, amplitude, frames, eye_fn, fovy=60.0, zne
             cv.copy_(torch.from_numpy(np.ascontiguousarray(colors, np.uint32).view(np.int32)))
         if launch:
             ctx.set_launch(*launch)
+        if bound_shift is not None:
+            ctx.set_depth_bound_split(bound_shift)
         ctx.set_sim(seed, cloud, amplitude, first_step)
         ctx.set_style(color, background)
         for f in range(frames):

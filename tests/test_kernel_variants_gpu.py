@@ -76,14 +76,14 @@ def test_render_paths(variant, mode, dtype):
                  f"{variant} {mode} {dtype}")
 
 
-def test_auto_picks_depth_bounds_for_dense_clouds_and_counts_launches():
-    """The default kernel choice: depth bounds (four launches per frame) from
-    2^20 points and four points per pixel, the direct splat (two) below."""
+def test_default_kernel_and_launch_counts():
+    """The default kernel for 1-px points is the direct splat (two launches
+    per frame); depth bounds chosen explicitly take four."""
     import torch
 
     from paper_2504_20937_b300.api import Context
     from ._harness import CENTRE, UP, upload
-    cases = [((1 << 20), 256, 128, 4), ((1 << 20), 1024, 512, 2), (100_000, 16, 16, 2)]
+    cases = [((1 << 20), 256, 128, 2), ((1 << 20), 1024, 512, 2), (100_000, 16, 16, 2)]
     for n, W, H, want in cases:
         stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 35, components=4, sigma=0.02), "f32")
         with Context(W, H) as ctx:
@@ -94,18 +94,19 @@ def test_auto_picks_depth_bounds_for_dense_clouds_and_counts_launches():
             ctx.step_and_render()
             torch.cuda.synchronize()
             assert ctx.last_frame_kernels() == want, (n, W, H)
-            ctx.set_launch(64, 0, "grid")
+            ctx.set_launch(64, 0, "depth_bound")
             ctx.step_and_render()
-            assert ctx.last_frame_kernels() == 2
-    # and the default choice renders what the oracle renders
+            assert ctx.last_frame_kernels() == 4
+    # first-pass shares of one half to 1/1024, every frame against the oracle
     n = 1 << 20
     stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 36, components=4, sigma=0.02), "f32")
     keep = {0, 1, 2}
     args = (stored, "f32", 256, 128, 3, 5e-4, 3, fixed_eye)
-    g = gpu_run(*args, keep_every=keep)
     o = oracle_run(*args, keep_every=keep)
-    _assert_same(g, o, "auto")
-    _kept_same(g, o, keep)
+    for shift in (1, 5, 10):
+        g = gpu_run(*args, keep_every=keep, launch=(64, 0, 2), bound_shift=shift)
+        _assert_same(g, o, f"shift {shift}")
+        _kept_same(g, o, keep)
 
 
 @pytest.mark.parametrize("variant", list(VARIANTS))
@@ -191,11 +192,11 @@ def test_disc_markers_with_tile_bounds(dtype, radius):
 
 
 def test_disc_markers_auto_choice():
-    """The default kernel bounds discs when n pi r^2 >= 16 W H (and n >= 2^20)."""
+    """The default kernel bounds discs when n pi r^2 >= 256 W H (and n >= 2^20)."""
     n = 1 << 20
     stored = inputs.encode(inputs.uniform_cloud(n, 39), "f32")
-    # 2^20 pi r^2 / (W H): 12.6 discs per pixel (direct), then 181 (bounded)
-    for radius, W, H, want in ((0.5, 256, 256, 2), (1.5, 256, 160, 4)):
+    # 2^20 pi r^2 / (W H): 181 discs per pixel (direct), then 322 (bounded)
+    for radius, W, H, want in ((1.5, 256, 160, 2), (2.0, 256, 160, 4)):
         gpos, gkeys, launches = _disc_run(stored, "f32", W, H, radius, 2, None)
         assert launches == want, radius
         pos, keys = _disc_oracle(stored, "f32", W, H, radius, 2)
