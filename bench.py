@@ -554,8 +554,10 @@ def run_c2_leg(make_ctx, timed_frames, hbm_gbs, frames=200):
 def run_features(sc, stored, hbm_gbs, frames=50):
     """The same 2^22-point 1920x1080 orbit with the paper's other usage
     patterns: ping-pong buffers (step out of place into the other buffer),
-    indexed colour (colormap[index[id]]), and disc markers of radius 1, 2
-    and 4 pixels.  Per-frame CUDA events, L2 flushed by a 512 MB read."""
+    indexed colour (colormap[index[id]]), and disc markers of radius 1, 2,
+    4, 8 and 16 pixels (the library's kernel choice: from 64 discs over each
+    pixel, two passes around 32x32-tile depth bounds).  Per-frame CUDA
+    events, L2 flushed by a 512 MB read."""
     import torch
     from paper_2504_20937_b300.api import Context
     dev = torch.cuda.current_device()
@@ -578,10 +580,11 @@ def run_features(sc, stored, hbm_gbs, frames=50):
             if f >= 3:
                 ms.append(a.elapsed_time(b))
         m = statistics.mean(ms)
-        return {"ms_per_frame": m, "points_per_s": sc.n / (m / 1e3), "p99_ms": float(np.percentile(ms, 99))}
+        return {"ms_per_frame": m, "points_per_s": sc.n / (m / 1e3), "p99_ms": float(np.percentile(ms, 99)),
+                "launches_per_frame": ctx.last_frame_kernels()}
 
     cases = [("pingpong", 0.0, False, True), ("indexed_colour", 0.0, True, False)]
-    cases += [(f"disc_r{r:g}", r, False, False) for r in (1.0, 2.0, 4.0)]
+    cases += [(f"disc_r{r:g}", r, False, False) for r in (1.0, 2.0, 4.0, 8.0, 16.0)]
     for name, radius, indexed, pingpong in cases:
         with Context(sc.W, sc.H) as ctx:
             if pingpong:

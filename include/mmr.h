@@ -181,8 +181,9 @@ MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t backgrou
  *    read when they lie behind their tile's bound (they could not win any of
  *    its pixels).  Three point-phase launches; 16 bytes per tile of device
  *    memory, allocated at the first such frame.  mmr_set_depth_bound_split
- *    sets the first pass's share of the points to 2^-shift (1..10, default
- *    3: one eighth), for 1-px points and disc markers alike.
+ *    sets the first pass's share of the points to 2^-shift (1..10; 0 for
+ *    the library's choice: one eighth, one sixteenth for discs covering
+ *    each pixel 1024 times or more), for 1-px points and disc markers alike.
  *  kernel = MMR_KERNEL_WARP_AGG: the grid-stride kernel whose lanes that hit
  *    the same pixel in one step elect their nearest point, which alone reads
  *    the key and takes the atomic.
@@ -190,9 +191,10 @@ MMR_API mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t backgrou
  *    thread per group) for 1-px points.
  * Disc markers (mmr_set_marker) use their own grid-stride kernel (64
  * threads).  Under MMR_KERNEL_DEPTH_BOUND, or MMR_KERNEL_AUTO with at least
- * 2^20 points and 256 discs over each pixel on average (n pi r^2 >= 256 w h),
+ * 2^20 points and 64 discs over each pixel on average (n pi r^2 >= 64 w h),
  * it runs in two passes with depth bounds of 32x32-pixel tiles between them:
- * a later disc behind the bounds of every tile it touches is skipped.
+ * a later disc behind the bounds of every tile it touches is skipped, and
+ * the discs that remain are drawn by whole warps, one disc at a time.
  * Results never depend on the shape or the kernel; only speed does. */
 enum mmr_kernel {
     MMR_KERNEL_GRID = 0,

@@ -191,12 +191,29 @@ bool uses_tma(const mmr::LaunchShape &ls) { return ls.kernel == MMR_KERNEL_TMA; 
 uint64_t tile_bytes(uint64_t tiles) { return 16 * tiles + 16; }
 
 // The depth-bound path pays for disc markers where many discs cover each
-// pixel: at least kDiscCoverMin on average (n pi r^2 / pixels, measured on the
-// 2^22-point 1080p orbit: r = 16, 1600 discs per pixel, 5.86 -> 2.05 ms; r = 4,
-// 100 per pixel, 0.42 -> 0.45 ms), for clouds of at least 2^20 points.  For
-// 1-px points it is chosen only explicitly: on the 64M-point 16-cluster 4K
-// frame it saved 1% in FP32 and cost 9-11% in 16-bit storage.
-constexpr double kDiscCoverMin = 256.0;
+// pixel: at least kDiscCoverMin on average (n pi r^2 / pixels), for clouds of
+// at least 2^20 points.  Measured on the 2^22-point 1080p orbit (direct ->
+// bounded, first pass 1/8): r = 2, 25 discs per pixel, 0.154 -> 0.263 ms;
+// r = 4, 100 per pixel, 0.42 -> 0.23 ms; r = 8, 400, 1.52 -> 0.35 ms; r = 16,
+// 1600, 5.86 -> 0.96 ms (0.80 ms with a first pass of 1/16).  For 1-px points
+// it is chosen only explicitly: on the 64M-point 16-cluster 4K frame it cost
+// 8% in FP32 and 9% in binary16, at every first-pass share tried.
+constexpr double kDiscCoverMin = 64.0;
+
+double discs_per_pixel(const mmr_ctx *c)
+{
+    return (double)c->n * 3.14159265358979 * c->disc_r * c->disc_r / (double)frame_px(c);
+}
+
+// The first pass's share, 2^-shift: as set by mmr_set_depth_bound_split,
+// else 1/16 for discs covering each pixel a thousand times or more and 1/8
+// otherwise (the fastest of 1/4 .. 1/64 measured at r = 4, 8 and 16).
+int bound_shift(const mmr_ctx *c)
+{
+    if (c->launch.bound_shift > 0)
+        return c->launch.bound_shift;
+    return c->disc_r > 0.0f && discs_per_pixel(c) >= 1024.0 ? 4 : 3;
+}
 
 bool uses_depth_bound(const mmr_ctx *c)
 {
@@ -205,8 +222,8 @@ bool uses_depth_bound(const mmr_ctx *c)
     if (c->launch.kernel != MMR_KERNEL_AUTO || c->n < (1ull << 20))
         return false;
     if (c->disc_r > 0.0f)
-        return (double)c->n * 3.14159265358979 * c->disc_r * c->disc_r >= kDiscCoverMin * (double)frame_px(c);
-    return false;     // 1-px points: the direct splat (see the measurements in the design notes)
+        return discs_per_pixel(c) >= kDiscCoverMin;
+    return false;     // 1-px points: the direct splat
 }
 
 // The tile arrays of the depth-bound path, allocated (zero-filled: no tile
@@ -269,7 +286,7 @@ cudaError_t launch_point_kernel(mmr_ctx *c, const void *src, void *dst, const mm
             // the 32x32-tile bounds live in the fine tiles' bound array, which is more than large enough
             mmr::DiscBounds T{fine.bound, fine.tag, (uint32_t)((c->W + 31) / 32), (uint32_t)((c->H + 31) / 32)};
             c->last_frame_kernels = 3;
-            return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, &T, c->launch.bound_shift,
+            return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, &T, bound_shift(c),
                                            c->launch.sm_count, s);
         }
         return mmr::launch_points_disc(c->dtype, src, dst, (uint32_t)c->n, P, displace, nullptr, 0,
@@ -284,8 +301,10 @@ cudaError_t launch_point_kernel(mmr_ctx *c, const void *src, void *dst, const mm
         if (e != cudaSuccess)
             return e;
         c->last_frame_kernels = 3;
-        return mmr::launch_points_bounded(c->dtype, src, dst, (uint32_t)c->n, P, displace, T, (uint32_t)c->tiles,
-                                          c->launch, s);
+        mmr::LaunchShape ls = c->launch;
+        ls.bound_shift = bound_shift(c);
+        return mmr::launch_points_bounded(c->dtype, src, dst, (uint32_t)c->n, P, displace, T, (uint32_t)c->tiles, ls,
+                                          s);
     }
     mmr::LaunchShape ls = c->launch;
     if (ls.kernel != MMR_KERNEL_WARP_AGG)
@@ -904,8 +923,8 @@ mmr_status mmr_set_depth_bound_split(mmr_ctx *ctx, int first_pass_shift)
 {
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
-    if (first_pass_shift < 1 || first_pass_shift > 10)
-        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_depth_bound_split: shift %d outside 1..10", first_pass_shift);
+    if (first_pass_shift < 0 || first_pass_shift > 10)
+        return fail(ctx, MMR_ERR_INVALID_ARG, "mmr_set_depth_bound_split: shift %d outside 0..10", first_pass_shift);
     ctx->launch.bound_shift = first_pass_shift;
     return MMR_OK;
 }

@@ -98,6 +98,44 @@ __device__ __forceinline__ bool disc_behind_bounds(const DiscBox &b, uint32_t de
     return true;
 }
 
+// The discs of a warp that survived the culling, splatted one at a time by
+// the whole warp: every lane calls this (mine = whether its disc is to be
+// drawn, with that disc's centre, key and candidate box), each surviving
+// disc's parameters are broadcast from its lane, and the lanes share the
+// disc's candidate pixels, consecutive lanes on consecutive pixels of a row
+// (coalesced depth reads).  Candidate t of a box w pixels wide is at row
+// floor(t / w), taken as the high half of t * ceil(2^32 / w), which equals
+// floor(t / w) for t < 2^32 / w (here t < 129 * 129).  The pixel test is
+// splat_disc's, in the same FP32 operations and order.
+__device__ __forceinline__ void splat_discs_by_warp(bool mine, float sx, float sy, unsigned long long key,
+                                                    const DiscBox &b, const PointParams &P)
+{
+    const unsigned full = 0xffffffffu;
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned todo = __ballot_sync(full, mine);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float dsx = __shfl_sync(full, sx, src), dsy = __shfl_sync(full, sy, src);
+        const unsigned long long dkey = __shfl_sync(full, key, src);
+        const int x0 = __shfl_sync(full, b.x0, src), x1 = __shfl_sync(full, b.x1, src);
+        const int y0 = __shfl_sync(full, b.y0, src), y1 = __shfl_sync(full, b.y1, src);
+        const uint32_t w = (uint32_t)(x1 - x0 + 1), npx = w * (uint32_t)(y1 - y0 + 1);
+        const uint64_t m = ((1ull << 32) + w - 1) / w;
+        for (uint32_t t = lane; t < npx; t += 32) {
+            const uint32_t row = (uint32_t)(((uint64_t)t * m) >> 32);
+            const int px = x0 + (int)(t - row * w), py = y0 + (int)row;
+            const float dy = __fsub_rn(__fadd_rn((float)py, 0.5f), dsy);
+            const float dx = __fsub_rn(__fadd_rn((float)px, 0.5f), dsx);
+            if (__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)) <= P.disc_r2) {
+                unsigned long long *k = P.keys + (uint32_t)py * (uint32_t)P.W + (uint32_t)px;
+                if (dkey < __ldca(k))
+                    atomicMin(k, dkey);
+            }
+        }
+    }
+}
+
 // One warp per tile, grid-stride over all tiles: lane l takes column l of
 // each of the tile's rows.  Pixels outside the frame are left out: no disc
 // reaches them (candidate boxes are clipped to the frame), and every tile

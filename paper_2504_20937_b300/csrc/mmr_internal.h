@@ -33,7 +33,8 @@ struct LaunchShape {
     int ctas_per_sm = 0;     // 0: one thread per work item; else a persistent grid
     int sm_count = 148;
     int kernel = kKernelGrid;
-    int bound_shift = 3;     // depth-bound variant: the first pass takes groups >> bound_shift groups
+    int bound_shift = 0;     // depth-bound variants: the first pass takes groups >> bound_shift groups (0: the
+                             // library's choice)
 };
 
 // Point kernels read positions from src and write displaced ones to dst

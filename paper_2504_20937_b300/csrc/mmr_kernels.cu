@@ -147,11 +147,10 @@ __global__ void tile_bound_kernel(const unsigned long long *__restrict__ keys, i
 
 // Disc markers: as points_kernel (one thread per 48-byte group, groups
 // g_begin .. g_end - 1), each point splatted as a disc of radius P.disc_r
-// pixels instead of one pixel.  With kCull, a disc that lies behind the depth
-// bounds of every tile its candidate box touches is skipped (mmr_disc.cuh).
-template <int DT, bool kDisplace, bool kCull>
+// pixels instead of one pixel, by its own thread.
+template <int DT, bool kDisplace>
 __global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
-                                   PointParams P, DiscBounds T)
+                                   PointParams P)
 {
     enter_dependent_grid();
     constexpr int G = Group<DT>::kPoints;
@@ -183,15 +182,77 @@ __global__ void points_disc_kernel(const void *src, void *dst, uint32_t n, uint3
                     v[3 * j + c] = storage_round<DT>(v[3 * j + c]);
             }
             float sx, sy, cw;
-            if (project_screen(v[3 * j], v[3 * j + 1], v[3 * j + 2], P, sx, sy, cw)) {
-                const DiscBox box = disc_box(sx, sy, P);
-                if (kCull && disc_behind_bounds(box, __float_as_uint(cw), T))
-                    continue;
-                splat_disc(sx, sy, depth_key(cw, P.id_base + i0 + j), P, box);
-            }
+            if (project_screen(v[3 * j], v[3 * j + 1], v[3 * j + 2], P, sx, sy, cw))
+                splat_disc(sx, sy, depth_key(cw, P.id_base + i0 + j), P);
         }
         if constexpr (kDisplace) {
             if (g < full) {
+#pragma unroll
+                for (int k = 0; k < 3 * G; ++k)
+                    set_word_coord<DT>(q, k, v[k]);
+                store_words(dst, g, q);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3 * G; ++k)
+                    if ((uint32_t)k < 3 * count)
+                        store_coord<DT>(dst, 3ull * i0 + k, v[k]);
+            }
+        }
+    }
+}
+
+// The culled disc pass: as points_disc_kernel, but the grid-stride loop
+// advances whole warps together (lane l of a warp takes group base + l, lanes
+// past g_end take no points), so every lane of a warp is present when the
+// discs that survive the tile bounds are splatted by the whole warp
+// (splat_discs_by_warp).  Discs behind their tiles' bounds are dropped.
+template <int DT, bool kDisplace>
+__global__ void points_disc_culled_kernel(const void *src, void *dst, uint32_t n, uint32_t g_begin, uint32_t g_end,
+                                          PointParams P, DiscBounds T)
+{
+    enter_dependent_grid();
+    constexpr int G = Group<DT>::kPoints;
+    const uint32_t full = n / G;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t gw = g_begin + blockIdx.x * blockDim.x + (threadIdx.x & ~31u); gw < g_end; gw += stride) {
+        const uint32_t g = gw + lane;
+        const uint32_t i0 = g * G;
+        const uint32_t count = g < g_end ? min((uint32_t)G, n - i0) : 0u;
+        uint4 q[3];
+        float v[3 * G];
+        if (g < full && g < g_end) {
+            load_words(src, g, q);
+#pragma unroll
+            for (int k = 0; k < 3 * G; ++k)
+                v[k] = word_coord<DT>(q, k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3 * G; ++k)
+                v[k] = (uint32_t)(k / 3) < count ? load_coord<DT>(src, 3ull * i0 + k) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const bool in = (uint32_t)j < count;
+            if constexpr (kDisplace) {
+                if (in) {
+                    displace_point(v[3 * j], v[3 * j + 1], v[3 * j + 2], i0 + j, P);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        v[3 * j + c] = storage_round<DT>(v[3 * j + c]);
+                }
+            }
+            float sx = 0.0f, sy = 0.0f, cw = 0.0f;
+            bool draw = in && project_screen(v[3 * j], v[3 * j + 1], v[3 * j + 2], P, sx, sy, cw);
+            DiscBox box{1, 0, 1, 0};
+            if (draw) {
+                box = disc_box(sx, sy, P);
+                draw = !disc_behind_bounds(box, __float_as_uint(cw), T);
+            }
+            splat_discs_by_warp(draw, sx, sy, depth_key(cw, P.id_base + i0 + j), box, P);
+        }
+        if constexpr (kDisplace) {
+            if (g < full && g < g_end) {
 #pragma unroll
                 for (int k = 0; k < 3 * G; ++k)
                     set_word_coord<DT>(q, k, v[k]);
@@ -219,9 +280,16 @@ static cudaError_t launch_disc_range(const void *src, void *dst, uint32_t n, uin
 {
     const uint64_t groups = g_end - g_begin;
     const int grid = (int)std::max<uint64_t>(1, (groups + 63) / 64);
-    if (displace)
-        return launch_dependent(points_disc_kernel<DT, true, kCull>, grid, 64, s, src, dst, n, g_begin, g_end, P, T);
-    return launch_dependent(points_disc_kernel<DT, false, kCull>, grid, 64, s, src, dst, n, g_begin, g_end, P, T);
+    if constexpr (kCull) {
+        if (displace)
+            return launch_dependent(points_disc_culled_kernel<DT, true>, grid, 64, s, src, dst, n, g_begin, g_end, P,
+                                    T);
+        return launch_dependent(points_disc_culled_kernel<DT, false>, grid, 64, s, src, dst, n, g_begin, g_end, P, T);
+    } else {
+        if (displace)
+            return launch_dependent(points_disc_kernel<DT, true>, grid, 64, s, src, dst, n, g_begin, g_end, P);
+        return launch_dependent(points_disc_kernel<DT, false>, grid, 64, s, src, dst, n, g_begin, g_end, P);
+    }
 }
 
 template <int DT>

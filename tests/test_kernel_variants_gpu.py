@@ -192,11 +192,12 @@ def test_disc_markers_with_tile_bounds(dtype, radius):
 
 
 def test_disc_markers_auto_choice():
-    """The default kernel bounds discs when n pi r^2 >= 256 W H (and n >= 2^20)."""
+    """The default kernel bounds discs when n pi r^2 >= 64 W H (and n >= 2^20),
+    with a first pass of 1/16 from 1024 discs per pixel."""
     n = 1 << 20
     stored = inputs.encode(inputs.uniform_cloud(n, 39), "f32")
-    # 2^20 pi r^2 / (W H): 181 discs per pixel (direct), then 322 (bounded)
-    for radius, W, H, want in ((1.5, 256, 160, 2), (2.0, 256, 160, 4)):
+    # 2^20 pi r^2 / (W H): 20 discs per pixel (direct), 181 and 1448 (bounded)
+    for radius, W, H, want in ((0.5, 256, 160, 2), (1.5, 256, 160, 4), (4.0, 256, 160, 4)):
         gpos, gkeys, launches = _disc_run(stored, "f32", W, H, radius, 2, None)
         assert launches == want, radius
         pos, keys = _disc_oracle(stored, "f32", W, H, radius, 2)
