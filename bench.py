@@ -43,6 +43,7 @@ from paper_2504_20937_b300 import inputs  # noqa: E402
 METRIC = "points/s (displace+render)"
 FLUSH_BYTES = 512 << 20
 L2_BYTES = 126 << 20
+TIMING_RING = 4096          # frames whose kernel times the library keeps (MMR_TIMING_RING)
 CENTRE = (0.5, 0.5, 0.5)
 UP = (0.0, 1.0, 0.0)
 
@@ -275,11 +276,24 @@ def run_ours(args, rank, world, local):
     def timed_frames(ctx, scene, frames, warm, do_flush, roundtrip=None, kernel_times=False):
         """Per-frame device times (ms) of the whole step and, with
         kernel_times (the library's per-kernel events switched on), of the
-        point and resolve phases.  The events between the phases cost about
-        5 us per frame, so whole-step times are taken with them off."""
+        point phase and the resolve.  The warm-up frames run and finish
+        first; then all timed frames are enqueued back to back, each between
+        two CUDA events on the launching stream (after its L2 flush, when
+        flushing), and read once the last one has finished, so the GPU is
+        never idle waiting for the host between frames."""
         ctx.set_timing(kernel_times)
-        step_ms, point_ms, resolve_ms = [], [], []
-        for f in range(warm + frames):
+        for f in range(warm):
+            ctx.set_camera(scene.eye(f), CENTRE, UP, scene.fovy_deg, scene.znear, scene.zfar)
+            if do_flush:
+                flush_sink.copy_(flush.sum())
+            if roundtrip is None:
+                ctx.step_and_render(stream)
+            else:
+                ctx.step_and_render_roundtrip(stream, pinned=roundtrip)
+        torch.cuda.synchronize()
+        ctx.set_timing(kernel_times)           # restarts the library's count: frames_back below are timed frames
+        marks = []
+        for f in range(warm, warm + frames):
             ctx.set_camera(scene.eye(f), CENTRE, UP, scene.fovy_deg, scene.znear, scene.zfar)
             if do_flush:
                 flush_sink.copy_(flush.sum())     # reads 512 MB: evicts L2 without dirtying it
@@ -291,12 +305,14 @@ def run_ours(args, rank, world, local):
             else:
                 ctx.step_and_render_roundtrip(stream, pinned=roundtrip)
             b.record(stream)
-            pk, rk = ctx.last_kernel_ms() if kernel_times else (0.0, 0.0)
-            b.synchronize()
-            if f >= warm:
-                step_ms.append(a.elapsed_time(b))
-                point_ms.append(pk)
-                resolve_ms.append(rk)
+            marks.append((a, b))
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in marks]
+        point_ms, resolve_ms = [0.0] * frames, [0.0] * frames
+        if kernel_times:
+            kept = min(frames, TIMING_RING)
+            times = [ctx.frame_kernel_ms(k) for k in range(kept)][::-1]      # oldest kept frame first
+            point_ms, resolve_ms = [t[0] for t in times], [t[1] for t in times]
         return step_ms, point_ms, resolve_ms
 
     storage = args.storage
@@ -309,19 +325,20 @@ def run_ours(args, rank, world, local):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
+        # the timed region: K frames, each bracketed by CUDA events on the launching stream, with the
+        # library's events around the point phase and the resolve of the same frames (the kernel durations
+        # of the roofline come from the timed region itself)
         t0 = time.perf_counter()
-        step_ms, _, _ = timed_frames(ctx, sc, args.steps, args.warmup, do_flush)
+        step_ms, point_ms, resolve_ms = timed_frames(ctx, sc, args.steps, args.warmup, do_flush, kernel_times=True)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        # four more repeats of the same K frames: the spread between repeats (`value` is the first)
+        kernel_frames = args.steps
+        # four more repeats of the same K frames without the kernel events: the spread between repeats and
+        # what the events cost (`value` is the timed region's)
         repeat_ms = [sum(step_ms) / args.steps]
         for _ in range(4):
             r_ms, _, _ = timed_frames(ctx, sc, args.steps, 0, do_flush)
             repeat_ms.append(sum(r_ms) / args.steps)
-        # the per-kernel durations: a second pass of the same frames with the library's events between the
-        # kernels, still under the clock sampler (stopping it perturbs the next few hundred milliseconds)
-        kernel_frames = min(args.steps, 200)
-        _, point_ms, resolve_ms = timed_frames(ctx, sc, kernel_frames, 3, do_flush, kernel_times=True)
     launches_per_frame = ctx.last_frame_kernels()
     total_ms = reduce_max(sum(step_ms))
     if world > 1:
@@ -368,11 +385,11 @@ def run_ours(args, rank, world, local):
         "kernels_ms": {"point_phase": mean_point_ms, "resolve": statistics.mean(resolve_ms),
                        "launches_per_frame": launches_per_frame,
                        "frames": kernel_frames,
-                       "note": "CUDA events around each kernel, in a second pass after the timed region: events "
-                               "between the kernels add about 5 us per frame, so the timed region runs without them"},
+                       "note": "the library's CUDA events around the point phase and the resolve of every frame of "
+                               "the timed region"},
         "repeats": {"ms_per_step": repeat_ms, "median_ms_per_step": float(np.median(repeat_ms)),
-                    "note": "the timed region and four more runs of the same K frames, timed the same way; "
-                            "value is the first"},
+                    "note": "the timed region (with the per-kernel events) and four more runs of the same K "
+                            "frames without them; value is the first"},
         "wall_s_timed_region": wall,
         "device_bytes": {"zero_copy": zero_copy_bytes, "zero_copy_cudaMemGetInfo": zero_copy_measured},
     }
@@ -567,7 +584,7 @@ def run_features(sc, stored, hbm_gbs, frames=50):
     res = {}
 
     def time_frames(ctx, step):
-        ms = []
+        marks = []
         for f in range(frames + 3):
             ctx.set_camera(sc.eye(f), CENTRE, UP, sc.fovy_deg, sc.znear, sc.zfar)
             sink.copy_(flush.sum())
@@ -576,9 +593,10 @@ def run_features(sc, stored, hbm_gbs, frames=50):
             a.record(stream)
             step(ctx)
             b.record(stream)
-            b.synchronize()
             if f >= 3:
-                ms.append(a.elapsed_time(b))
+                marks.append((a, b))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in marks]
         m = statistics.mean(ms)
         return {"ms_per_frame": m, "points_per_s": sc.n / (m / 1e3), "p99_ms": float(np.percentile(ms, 99)),
                 "launches_per_frame": ctx.last_frame_kernels()}

@@ -274,11 +274,19 @@ MMR_API mmr_status mmr_last_frame_kernels(const mmr_ctx *ctx, int *kernels);
 MMR_API mmr_status mmr_get_step(const mmr_ctx *ctx, uint32_t *step);
 
 /* Per-kernel timing for benchmarks.  When enabled, the library records CUDA
- * events on the frame's stream around the point kernel and the resolve
- * kernel of every frame; mmr_last_kernel_ms waits for the latest frame's
- * events and returns both durations in milliseconds (either pointer may be
- * NULL).  MMR_ERR_STATE if timing is off or no frame was timed yet. */
+ * events on the frame's stream before the point phase, between it and the
+ * resolve and after the resolve of every frame, and keeps them for the last
+ * MMR_TIMING_RING frames, so that many frames can be enqueued back to back
+ * and timed afterwards.  mmr_frame_kernel_ms waits for the events of the
+ * frame `frames_back` frames before the latest (0 = the latest) and returns
+ * both durations in milliseconds (either pointer may be NULL);
+ * mmr_last_kernel_ms is the latest frame's.  MMR_ERR_STATE if timing is off
+ * or that frame was not timed or is no longer kept.  Switching timing on
+ * restarts the count.  The events between the point phase and the resolve
+ * cost a few microseconds per frame. */
+#define MMR_TIMING_RING 4096u
 MMR_API mmr_status mmr_set_timing(mmr_ctx *ctx, int enable);
+MMR_API mmr_status mmr_frame_kernel_ms(mmr_ctx *ctx, uint32_t frames_back, float *point_ms, float *resolve_ms);
 MMR_API mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *resolve_ms);
 
 /* Synchronise the device and report whether a kernel of this context gave

@@ -58,6 +58,7 @@ SIGNATURES = {
     "mmr_frame_ptr": (_i, [_vp, C.POINTER(_vp), C.POINTER(_vp)]),
     "mmr_get_step": (_i, [_vp, C.POINTER(_u32)]),
     "mmr_last_frame_kernels": (_i, [_vp, C.POINTER(_i)]),
+    "mmr_frame_kernel_ms": (_i, [_vp, _u32, C.POINTER(_f), C.POINTER(_f)]),
     "mmr_set_depth_bound_split": (_i, [_vp, _i]),
     "mmr_set_timing": (_i, [_vp, _i]),
     "mmr_check_device": (_i, [_vp]),

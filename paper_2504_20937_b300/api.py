@@ -203,9 +203,16 @@ class Context:
         self._check(self._lib.mmr_set_timing(self._h, int(enable)))
 
     def last_kernel_ms(self):
-        """(point kernel ms, resolve kernel ms) of the latest timed frame."""
+        """(point phase ms, resolve ms) of the latest timed frame."""
         a, b = C.c_float(), C.c_float()
         self._check(self._lib.mmr_last_kernel_ms(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def frame_kernel_ms(self, frames_back: int):
+        """(point phase ms, resolve ms) of the timed frame `frames_back`
+        frames before the latest (waits for it)."""
+        a, b = C.c_float(), C.c_float()
+        self._check(self._lib.mmr_frame_kernel_ms(self._h, frames_back, C.byref(a), C.byref(b)))
         return a.value, b.value
 
     def set_depth_bound_split(self, first_pass_shift: int = 3):

@@ -72,14 +72,19 @@ struct mmr_ctx {
     uint32_t background = 0u;
     float disc_r = 0.0f;          // 0: 1-px points; else disc markers of this radius (pixels)
 
+    // per-kernel timing: a ring of event triples (before the point phase, between it and the resolve, after
+    // the resolve), one triple per frame, so a caller can enqueue many frames and read their times afterwards
     bool timing = false;
-    bool timed_frame = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    uint32_t timed_frames = 0;                 // frames timed since timing was switched on
+    cudaEvent_t *ring = nullptr;               // kTimingRing * 3 events
+    cudaEvent_t *ev = nullptr;                 // the triple of the frame being enqueued
 
     char err[512] = "";
 };
 
 namespace {
+
+constexpr uint32_t kTimingRing = MMR_TIMING_RING;
 
 mmr_status fail(mmr_ctx *c, mmr_status s, const char *fmt, ...)
 {
@@ -322,8 +327,10 @@ mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStre
             return st;
     }
     mmr::PointParams P = point_params(c);
-    if (c->timing)
+    if (c->timing) {
+        c->ev = c->ring + 3 * (c->timed_frames % kTimingRing);
         cudaEventRecord(c->ev[0], s);
+    }
     cudaError_t e = launch_point_kernel(c, src, dst, P, displace, true, s);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "point kernel launch");
@@ -336,7 +343,7 @@ mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStre
         return cuda_fail(c, e, "resolve kernel launch");
     if (c->timing) {
         cudaEventRecord(c->ev[2], s);
-        c->timed_frame = true;
+        c->timed_frames += 1;
     }
     c->last_frame_kernels += 1;
     c->latest_buf = cur;
@@ -500,9 +507,12 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
         else
             free(ctx->rt_host);
     }
-    for (cudaEvent_t &ev : ctx->ev)
-        if (ev)
-            cudaEventDestroy(ev);
+    if (ctx->ring) {
+        for (uint32_t k = 0; k < 3 * kTimingRing; ++k)
+            if (ctx->ring[k])
+                cudaEventDestroy(ctx->ring[k]);
+        delete[] ctx->ring;
+    }
     delete ctx;
     return MMR_OK;
 }
@@ -644,8 +654,10 @@ mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt
     mmr::PointParams P = point_params(ctx);
     const mmr::NbodyParams B{G, eps2, dt};
     const int r = ctx->visible;
-    if (ctx->timing)
+    if (ctx->timing) {
+        ctx->ev = ctx->ring + 3 * (ctx->timed_frames % kTimingRing);
         cudaEventRecord(ctx->ev[0], s);
+    }
     cudaError_t e = mmr::launch_nbody(static_cast<const float *>(ctx->buf[r]), static_cast<float *>(ctx->buf[r ^ 1]),
                                       ctx->nb_vel, ctx->nb_mass, ctx->nb_partial, (uint32_t)ctx->n, B, P, s);
     if (e != cudaSuccess)
@@ -659,7 +671,7 @@ mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt
         return cuda_fail(ctx, e, "resolve kernel launch");
     if (ctx->timing) {
         cudaEventRecord(ctx->ev[2], s);
-        ctx->timed_frame = true;
+        ctx->timed_frames += 1;
     }
     ctx->latest_buf = cur;
     ctx->splat_buf = cur ^ 1;
@@ -949,15 +961,41 @@ mmr_status mmr_set_timing(mmr_ctx *ctx, int enable)
 {
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
-    if (enable && !ctx->ev[0]) {
-        for (cudaEvent_t &ev : ctx->ev) {
-            cudaError_t e = cudaEventCreate(&ev);
+    if (enable && !ctx->ring) {
+        ctx->ring = new (std::nothrow) cudaEvent_t[3 * kTimingRing]();
+        if (!ctx->ring)
+            return fail(ctx, MMR_ERR_OOM, "mmr_set_timing: host allocation failed");
+        for (uint32_t k = 0; k < 3 * kTimingRing; ++k) {
+            cudaError_t e = cudaEventCreate(&ctx->ring[k]);
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e, "mmr_set_timing: cudaEventCreate");
         }
     }
     ctx->timing = enable != 0;
-    ctx->timed_frame = false;
+    ctx->timed_frames = 0;
+    return MMR_OK;
+}
+
+mmr_status mmr_frame_kernel_ms(mmr_ctx *ctx, uint32_t frames_back, float *point_ms, float *resolve_ms)
+{
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (!ctx->timing || frames_back >= ctx->timed_frames || frames_back >= kTimingRing)
+        return fail(ctx, MMR_ERR_STATE, "mmr_frame_kernel_ms: timing off, or frame %u back not timed or no longer "
+                    "kept (%u timed, %u kept)", frames_back, ctx->timed_frames, kTimingRing);
+    const cudaEvent_t *t = ctx->ring + 3 * ((ctx->timed_frames - 1 - frames_back) % kTimingRing);
+    cudaError_t e = cudaEventSynchronize(t[2]);
+    float a = 0.0f, b = 0.0f;
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&a, t[0], t[1]);
+    if (e == cudaSuccess)
+        e = cudaEventElapsedTime(&b, t[1], t[2]);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_frame_kernel_ms");
+    if (point_ms)
+        *point_ms = a;
+    if (resolve_ms)
+        *resolve_ms = b;
     return MMR_OK;
 }
 
@@ -965,21 +1003,9 @@ mmr_status mmr_last_kernel_ms(mmr_ctx *ctx, float *point_ms, float *resolve_ms)
 {
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
-    if (!ctx->timing || !ctx->timed_frame)
+    if (!ctx->timing || ctx->timed_frames == 0)
         return fail(ctx, MMR_ERR_STATE, "mmr_last_kernel_ms: timing off or no timed frame yet");
-    cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
-    float a = 0.0f, b = 0.0f;
-    if (e == cudaSuccess)
-        e = cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]);
-    if (e == cudaSuccess)
-        e = cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e, "mmr_last_kernel_ms");
-    if (point_ms)
-        *point_ms = a;
-    if (resolve_ms)
-        *resolve_ms = b;
-    return MMR_OK;
+    return mmr_frame_kernel_ms(ctx, 0, point_ms, resolve_ms);
 }
 
 mmr_status mmr_check_device(mmr_ctx *ctx)

@@ -393,3 +393,27 @@ def test_disc_markers_at_exact_pixel_distances(radius, W, H, kernel):
     keys, _ = oracle.render_disc(pos, M.reshape(-1), W, H, np.float32(0.5), np.float32(2.0), np.float32(radius))
     assert np.array_equal(gkeys, keys), f"{np.count_nonzero(gkeys != keys)} pixels differ"
     assert (keys != oracle.EMPTY_KEY).sum() > W * H // 4
+
+
+def test_per_frame_kernel_timing_ring():
+    """Frames enqueued back to back keep their own kernel times; reading a
+    frame that was not timed, or after timing restarts, is refused."""
+    from paper_2504_20937_b300.api import Context, MmrError
+    n, W, H = 50_000, 64, 48
+    stored = inputs.encode(inputs.uniform_cloud(n, 41), "f32")
+    with Context(W, H) as ctx:
+        ctx.alloc_points(n, "f32").copy_(torch.from_numpy(stored))
+        ctx.set_camera((0.5, 0.5, 2.5), (0.5, 0.5, 0.5), (0, 1, 0), 60.0, 0.1, 100.0)
+        with pytest.raises(MmrError, match="STATE"):
+            ctx.last_kernel_ms()                      # timing is off
+        ctx.set_timing(True)
+        for _ in range(10):
+            ctx.step_and_render()
+        times = [ctx.frame_kernel_ms(k) for k in range(10)]
+        assert all(p > 0.0 and r > 0.0 for p, r in times)
+        assert ctx.last_kernel_ms() == times[0]
+        with pytest.raises(MmrError, match="STATE"):
+            ctx.frame_kernel_ms(10)
+        ctx.set_timing(True)                          # restarts the count
+        with pytest.raises(MmrError, match="STATE"):
+            ctx.frame_kernel_ms(0)
