@@ -107,7 +107,9 @@ static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int thre
 // finds 55 without spilling (at 56 it spills 8 bytes).  Measured on the
 // 64M-point 16-cluster 4K frame against the one-point projection at 47
 // registers, on one box: 444.5 -> 408.9 us (cap 56: 408.0 us with the spill,
-// cap 64: 414.3 us); the 2^22-point 1080p frame 43.8 -> 42.9 us.
+// cap 64: 414.3 us); the 2^22-point 1080p frame 43.8 -> 42.9 us.  Pairing the
+// displacement's offsets too (displace_pair), still 55 registers: 408.5 ->
+// 405.0 us and 43.1 -> 42.3 us on another box.
 // Groups g_begin .. g_end - 1; `splat` is the splat policy (mmr_points.cuh,
 // mmr_tiles.cuh).
 template <bool kDisplace, bool kSplat, typename Splat>

@@ -217,8 +217,9 @@ __device__ __forceinline__ void splat_packed(const uint4 (&q)[3], uint32_t i0, c
                     word_coord<DT>(q, 3 * j + 2), P.id_base + i0 + j);
 }
 
-// kPairs: project the points two at a time on packed FP32 pairs
-// (project_pixel2): fewer instructions, more registers.
+// kPairs (FP32): displace and project the points two at a time on packed
+// FP32 pairs (displace_pair, project_pixel2): fewer instructions, more
+// registers.
 template <int DT, bool kDisplace, bool kSplat, typename Splat = SplatDirect, bool kPairs = false>
 __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32_t count, const PointParams &P,
                                               const Splat &splat = Splat{})
@@ -228,7 +229,21 @@ __device__ __forceinline__ void process_words(uint4 (&q)[3], uint32_t i0, uint32
 #pragma unroll
     for (int k = 0; k < 3 * G; ++k)
         v[k] = word_coord<DT>(q, k);
-    if constexpr (kDisplace) {
+    if constexpr (kDisplace && kPairs && DT == kF32) {
+        // two points at a time (displace_pair); a point past `count` is displaced but not kept
+#pragma unroll
+        for (int j = 0; j < G; j += 2) {
+            float w[6] = {v[3 * j], v[3 * j + 1], v[3 * j + 2], v[3 * j + 3], v[3 * j + 4], v[3 * j + 5]};
+            displace_pair(w[0], w[1], w[2], i0 + j, w[3], w[4], w[5], i0 + j + 1, P);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                if ((uint32_t)(j + c / 3) < count) {
+                    v[3 * j + c] = w[c];
+                    set_word_coord<DT>(q, 3 * j + c, w[c]);
+                }
+            }
+        }
+    } else if constexpr (kDisplace) {
 #pragma unroll
         for (int j = 0; j < G; ++j) {       // constant indices keep q and v in registers
             if ((uint32_t)j < count) {
