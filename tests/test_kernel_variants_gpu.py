@@ -202,3 +202,34 @@ def test_disc_markers_auto_choice():
         assert launches == want, radius
         pos, keys = _disc_oracle(stored, "f32", W, H, radius, 2)
         assert np.array_equal(gpos, pos) and np.array_equal(gkeys[1], keys[1]), radius
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (7, 5), (32768, 32), (33, 4097)])
+def test_depth_bound_frame_shapes(W, H):
+    """Frames of one pixel, smaller than one tile, one tile row 4096 tiles
+    wide, and 4097 rows: every frame against the oracle, with the first pass
+    taking half the points so many tiles get bounds."""
+    n = 120_001
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 42, components=3, sigma=0.03), "f32")
+    keep = {0, 1}
+    args = (stored, "f32", W, H, 5, 1e-3, 2, orbit(4.0))
+    g = gpu_run(*args, launch=(64, 0, 2), keep_every=keep, bound_shift=1)
+    o = oracle_run(*args, keep_every=keep)
+    _assert_same(g, o, f"{W}x{H}")
+    _kept_same(g, o, keep)
+
+
+@pytest.mark.parametrize("dtype,radius,W,H", [("f32", 64.0, 200, 150), ("f32", 24.0, 1, 300), ("bf16", 8.0, 301, 7),
+                                              ("f16", 0.5, 90, 60)])
+def test_disc_tile_bounds_edges(dtype, radius, W, H):
+    """Disc markers with tile bounds where discs reach far past the frame
+    (r = 64: candidate boxes of 129 px over up to 5x5 tiles), a frame one
+    pixel wide, one seven rows high, and the smallest radius."""
+    n = 60_007
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(n, 43, components=2, sigma=0.1), dtype)
+    gpos, gkeys, launches = _disc_run(stored, dtype, W, H, radius, 2, "depth_bound")
+    pos, keys = _disc_oracle(stored, dtype, W, H, radius, 2)
+    assert launches == 4
+    assert np.array_equal(gpos.view(np.uint8), pos.view(np.uint8))
+    for f in range(2):
+        assert np.array_equal(gkeys[f], keys[f]), f"frame {f}: {np.count_nonzero(gkeys[f] != keys[f])} pixels differ"
