@@ -271,6 +271,7 @@ mmr::TileBounds next_tile_bounds(mmr_ctx *c, cudaStream_t s, cudaError_t *e)
     T.count = reinterpret_cast<uint32_t *>(c->tiles_mem + 16 * c->tiles);
     T.tag = c->tile_tag;
     T.tiles_w = c->tiles_w;
+    T.tiles = (uint32_t)c->tiles;
     return T;
 }
 

@@ -29,6 +29,7 @@ struct TileBounds {
     unsigned long long *bound;          // per tile: (tag << 32) | largest depth bits of its keys
     uint32_t tag;                       // this frame's tag (never 0)
     uint32_t tiles_w;                   // tiles per row
+    uint32_t tiles;                     // tiles of the frame: the list's capacity
 };
 
 __device__ __forceinline__ uint32_t tile_of(uint32_t ix, uint32_t iy, uint32_t tiles_w)
@@ -39,8 +40,10 @@ __device__ __forceinline__ uint32_t tile_of(uint32_t ix, uint32_t iy, uint32_t t
 // First pass: the direct splat, and a mark on the tile of every point that
 // performs an atomic.  The first point to mark a tile in this frame (the one
 // whose exchange returns another tag) appends the tile to the list, so a
-// tile is listed at most once per frame and the list never outgrows the
-// tile count.  A stale L1 copy of a mark costs at most one more exchange.
+// tile is listed at most once per frame and, as the second pass of every
+// frame empties the list, it never outgrows the tile count; the append is
+// bounded by the capacity all the same.  A stale L1 copy of a mark costs at
+// most one more exchange.
 struct SplatMarkTiles {
     static constexpr bool kWarpWide = false;
     TileBounds T;
@@ -54,8 +57,11 @@ struct SplatMarkTiles {
         if (key < __ldca(k)) {
             atomicMin(k, key);
             const uint32_t t = tile_of(ix, iy, T.tiles_w);
-            if (__ldca(T.mark + t) != T.tag && atomicExch(T.mark + t, T.tag) != T.tag)
-                T.list[atomicAdd(T.count, 1u)] = t;
+            if (__ldca(T.mark + t) != T.tag && atomicExch(T.mark + t, T.tag) != T.tag) {
+                const uint32_t slot = atomicAdd(T.count, 1u);
+                if (slot < T.tiles)
+                    T.list[slot] = t;
+            }
         }
     }
 };
@@ -121,7 +127,7 @@ __device__ __forceinline__ void tile_bound_body(const unsigned long long *__rest
 {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t count = *T.count;
+    const uint32_t count = min(*T.count, T.tiles);
     for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += warps) {
         const uint32_t t = T.list[i];
         const uint32_t x = (t % T.tiles_w) * 8u + 2u * (lane & 3u);
