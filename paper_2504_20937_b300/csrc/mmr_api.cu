@@ -440,7 +440,7 @@ mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx *
     c->budget = budget_bytes;
     c->launch.threads = 64;           // fastest measured shape (grid-stride, one thread per group)
     c->launch.ctas_per_sm = 0;
-    c->launch.kernel = MMR_KERNEL_AUTO;   // depth bounds for dense clouds, else the grid-stride kernel
+    c->launch.kernel = MMR_KERNEL_AUTO;   // depth bounds for dense disc markers, else the grid-stride kernel
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&c->launch.sm_count, cudaDevAttrMultiProcessorCount, c->device);
