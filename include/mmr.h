@@ -263,7 +263,10 @@ MMR_API mmr_status mmr_step_and_render_roundtrip(mmr_ctx *ctx, void *stream, int
  * straight from memory shared with the compute side instead of a host copy
  * (Sec. 1, Sec. 3.2.1).  Valid after the stream that rendered the frame is
  * synchronised, until the next frame or mmr_destroy.  Either output pointer
- * may be NULL. */
+ * may be NULL.  Both buffers are read-only to the caller: each resolve
+ * repaints only the runs of 64 pixels that its frame or the one before
+ * touched (elsewhere the framebuffer already holds the background), so a
+ * pixel the caller changed could stay changed. */
 MMR_API mmr_status mmr_frame_ptr(mmr_ctx *ctx, const uint32_t **rgba, const uint64_t **depth_id);
 
 /* Number of kernels the latest frame of this context launched (point phase

@@ -32,7 +32,13 @@ struct mmr_ctx {
     int splat_buf = 0;            // key buffer the next frame splats into
     int latest_buf = 0;           // key buffer holding the latest frame
     uint32_t *rgba = nullptr;
-    uint32_t *d_err = nullptr;    // device error word (bounded waits that gave up)
+    uint32_t *d_err = nullptr;    // device error word (bounded waits that gave up), at the start of the control
+                                  // block that also holds the frame-chunk tags
+    uint64_t ctrl_bytes = 0;
+    uint32_t *chunk_tags[2] = {nullptr, nullptr};  // per depth-id buffer: one tag per 64-pixel chunk (FrameChunks)
+    uint32_t frame_no = 0;        // number of the latest resolved frame (1, 2, ...)
+    uint32_t buf_frame[2] = {0, 0};   // number of the frame last resolved from each depth-id buffer
+    bool repaint_all = true;      // the next resolve repaints and clears every pixel
 
     void *buf[2] = {nullptr, nullptr};   // point buffers; buf[1] only with ping-pong
     int visible = 0;                     // the buffer holding the current state (rendered)
@@ -195,6 +201,37 @@ bool uses_tma(const mmr::LaunchShape &ls) { return ls.kernel == MMR_KERNEL_TMA; 
 
 uint64_t tile_bytes(uint64_t tiles) { return 16 * tiles + 16; }
 
+// Control block: the 4-byte device error word, padded to 16 bytes, then the
+// chunk tags of both depth-id buffers.
+uint64_t frame_chunks_of(const mmr_ctx *c) { return (frame_px(c) + 63) / 64; }
+uint64_t control_bytes(const mmr_ctx *c) { return 16 + 2 * 4 * frame_chunks_of(c); }
+
+// The chunk bookkeeping of the resolve that turns depth-id buffer `cur` into
+// the framebuffer and clears the other one.  Frame numbers run 1, 2, ...; tags
+// start at 0, which matches the "previous frame" of both buffers before any
+// frame, so the first resolve clears everything.  Before the numbers would
+// repeat the tags are cleared on the stream and counting starts again.
+mmr::FrameChunks frame_chunks(mmr_ctx *c, int cur, cudaStream_t s, cudaError_t *e)
+{
+    *e = cudaSuccess;
+    if (c->frame_no == 0xffffffffu) {
+        *e = cudaMemsetAsync(c->chunk_tags[0], 0, 2 * 4 * frame_chunks_of(c), s);
+        c->frame_no = 0;
+        c->buf_frame[0] = c->buf_frame[1] = 0;
+        c->repaint_all = true;
+    }
+    return mmr::FrameChunks{c->chunk_tags[cur ^ 1], c->chunk_tags[cur], c->buf_frame[cur ^ 1], c->frame_no + 1,
+                            c->repaint_all ? 1u : 0u};
+}
+
+// After the resolve of buffer `cur` is enqueued.
+void frame_resolved(mmr_ctx *c, int cur)
+{
+    c->frame_no += 1;
+    c->buf_frame[cur] = c->frame_no;
+    c->repaint_all = false;
+}
+
 // The depth-bound path pays for disc markers where many discs cover each
 // pixel: at least kDiscCoverMin on average (n pi r^2 / pixels), for clouds of
 // at least 2^20 points.  Measured on the 2^22-point 1080p orbit (direct ->
@@ -338,10 +375,12 @@ mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStre
     if (c->timing)
         cudaEventRecord(c->ev[1], s);
     const int cur = c->splat_buf;
-    e = mmr::launch_resolve(c->keys[cur], c->keys[cur ^ 1], c->rgba, palette(c), (uint32_t)frame_px(c), c->launch,
-                            s);
+    const mmr::FrameChunks F = frame_chunks(c, cur, s, &e);
+    if (e == cudaSuccess)
+        e = mmr::launch_resolve(c->keys[cur], c->keys[cur ^ 1], c->rgba, palette(c), (uint32_t)frame_px(c), F, s);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "resolve kernel launch");
+    frame_resolved(c, cur);
     if (c->timing) {
         cudaEventRecord(c->ev[2], s);
         c->timed_frames += 1;
@@ -456,10 +495,15 @@ mmr_status mmr_create_ex(int width, int height, uint64_t budget_bytes, mmr_ctx *
         st = dev_alloc(c, (void **)&c->keys[1], npx * 8, "depth-id buffer 1");
     if (st == MMR_OK)
         st = dev_alloc(c, (void **)&c->rgba, npx * 4, "RGBA framebuffer");
+    c->ctrl_bytes = control_bytes(c);
     if (st == MMR_OK)
-        st = dev_alloc(c, (void **)&c->d_err, 4, "device error word");
+        st = dev_alloc(c, (void **)&c->d_err, c->ctrl_bytes, "device error word and frame-chunk tags");
     if (st == MMR_OK) {
-        e = cudaMemset(c->d_err, 0, 4);
+        c->chunk_tags[0] = c->d_err + 4;
+        c->chunk_tags[1] = c->chunk_tags[0] + frame_chunks_of(c);
+        if (const char *v = getenv("MMR_FIRST_FRAME_NUMBER"))      // test hook: start near the wrap of the numbers
+            c->frame_no = (uint32_t)strtoul(v, nullptr, 0);
+        e = cudaMemset(c->d_err, 0, c->ctrl_bytes);
         if (e == cudaSuccess)
             e = cudaMemset(c->keys[0], 0xff, npx * 8);
         if (e == cudaSuccess)
@@ -491,7 +535,7 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
     dev_free(ctx, (void **)&ctx->keys[0], frame_px(ctx) * 8);
     dev_free(ctx, (void **)&ctx->keys[1], frame_px(ctx) * 8);
     dev_free(ctx, (void **)&ctx->rgba, frame_px(ctx) * 4);
-    dev_free(ctx, (void **)&ctx->d_err, 4);
+    dev_free(ctx, (void **)&ctx->d_err, ctx->ctrl_bytes);
     dev_free(ctx, &ctx->buf[0], storage_bytes(ctx->n, ctx->dtype));
     dev_free(ctx, &ctx->buf[1], storage_bytes(ctx->n, ctx->dtype));
     dev_free(ctx, (void **)&ctx->colors, ctx->n * 4);
@@ -666,10 +710,13 @@ mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt
     if (ctx->timing)
         cudaEventRecord(ctx->ev[1], s);
     const int cur = ctx->splat_buf;
-    e = mmr::launch_resolve(ctx->keys[cur], ctx->keys[cur ^ 1], ctx->rgba, palette(ctx), (uint32_t)frame_px(ctx),
-                            ctx->launch, s);
+    const mmr::FrameChunks F = frame_chunks(ctx, cur, s, &e);
+    if (e == cudaSuccess)
+        e = mmr::launch_resolve(ctx->keys[cur], ctx->keys[cur ^ 1], ctx->rgba, palette(ctx), (uint32_t)frame_px(ctx),
+                                F, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "resolve kernel launch");
+    frame_resolved(ctx, cur);
     if (ctx->timing) {
         cudaEventRecord(ctx->ev[2], s);
         ctx->timed_frames += 1;
@@ -795,6 +842,8 @@ mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background)
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     ctx->color = color;
+    if (background != ctx->background)
+        ctx->repaint_all = true;      // pixels left as background by earlier frames are repainted
     ctx->background = background;
     return MMR_OK;
 }

@@ -19,6 +19,7 @@ struct NvtxRange {
 struct PointParams;
 struct Palette;
 struct TileBounds;
+struct FrameChunks;
 
 // Point-kernel variants (the values of mmr_set_launch's `kernel`).
 enum : int {
@@ -68,8 +69,10 @@ cudaError_t launch_points_tma(int dtype, const void *src, void *dst, uint32_t n,
 // sets *err like a point kernel whose bulk copy never completed.
 cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cudaStream_t s);
 
+// Resolve keys into rgba and clear next_keys, storing only in the chunks
+// that F says this frame or the previous one touched (mmr_resolve.cuh).
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
-                           const Palette &pal, uint32_t npx, const LaunchShape &ls, cudaStream_t s);
+                           const Palette &pal, uint32_t npx, const FrameChunks &F, cudaStream_t s);
 
 // Displacement amplitudes the kernels accept: 0, or [2^-100, 1] (so that
 // amplitude * 2^-23 is a normal float and the scaling is exact).

@@ -47,6 +47,24 @@ __device__ __forceinline__ void resolve_quad(const unsigned long long *__restric
     reinterpret_cast<ulonglong2 *>(next_keys)[2 * q + 1] = e;
 }
 
+// Frame chunks of the single-cloud resolve: runs of 64 consecutive pixels
+// (16 quads), one 32-bit tag per chunk and depth-id buffer.  A resolve tags
+// every chunk in which its frame left a key with the frame's number.  The
+// next resolve, which clears that buffer for the frame after it, clears and
+// repaints only the chunks carrying the previous frame's number: elsewhere
+// the buffer holds no key, and the framebuffer already holds background
+// (painted by an earlier resolve and untouched since), unless this frame
+// puts a point there.  Skipping those stores changes no pixel.
+constexpr uint32_t kChunkQuadShift = 4;      // 16 quads = 64 pixels per chunk
+
+struct FrameChunks {
+    const uint32_t *prev;   // tags of the buffer being cleared (left by the previous frame's resolve)
+    uint32_t *cur;          // tags of the buffer being resolved
+    uint32_t prev_tag;      // the previous frame's number
+    uint32_t cur_tag;       // this frame's number
+    uint32_t full;          // non-zero: repaint and clear every chunk (first frame, new background)
+};
+
 __device__ __forceinline__ void resolve_pixel(const unsigned long long *__restrict__ keys,
                                               unsigned long long *__restrict__ next_keys,
                                               uint32_t *__restrict__ rgba, const Palette &pal, uint32_t p)
