@@ -51,6 +51,7 @@ struct CloudDev {
     uint32_t seed_lo, seed_hi, cloud;
     float amplitude;
     uint32_t color, background;
+    uint32_t *tags[2];          // per depth-id buffer: one tag per 64-pixel chunk (FrameChunks)
 };
 
 
@@ -65,7 +66,8 @@ struct BatchTables {
     uint32_t slots;
     uint32_t first_step;
     uint32_t spin_limit;        // polls before a pixel item gives up waiting
-    uint32_t *frame;            // device frame counter
+    uint32_t *frame;            // device frame counter, then the repaint flag (non-zero: the next frame repaints
+                                // and clears every pixel; the advance kernel resets it)
     uint32_t *next;             // next item to hand out, zeroed before every frame
     uint32_t *remaining;        // [count] unfinished point items per cloud, reset before every frame
     uint32_t *err;              // bit 0: a bounded wait gave up
@@ -137,18 +139,32 @@ constexpr int kBatchMaxThreads = 512;
 
 // Resolve + clear of four pixels with the keys read from L2 (ld.global.cg):
 // this SM's L1 may still hold lines of this cloud's keys from its own early
-// depth tests, older than the atomics that followed.
+// depth tests, older than the atomics that followed.  As in the single-cloud
+// resolve (FrameChunks), colours are stored and the other buffer cleared
+// only in 64-pixel chunks that this frame or the previous one touched; a
+// quad holding a key tags its chunk with this frame's number (lanes of a
+// warp storing the same tag to the same word make one store).
 __device__ __forceinline__ void resolve_quad_l2(const unsigned long long *keys, unsigned long long *next_keys,
-                                                uint32_t *rgba, const Palette &pal, uint32_t q)
+                                                uint32_t *rgba, const Palette &pal, uint32_t q,
+                                                const FrameChunks &F)
 {
     const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q);
     const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q + 1);
-    const uint4 c = make_uint4(key_colour(k01.x, pal), key_colour(k01.y, pal), key_colour(k23.x, pal),
-                               key_colour(k23.y, pal));
-    __stcs(reinterpret_cast<uint4 *>(rgba) + q, c);
-    const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
-    reinterpret_cast<ulonglong2 *>(next_keys)[2 * q] = e;
-    reinterpret_cast<ulonglong2 *>(next_keys)[2 * q + 1] = e;
+    const bool dirty = (k01.x & k01.y & k23.x & k23.y) != kEmptyKey;
+    const uint32_t chunk = q >> kChunkQuadShift;
+    const bool prev = F.full || __ldg(F.prev + chunk) == F.prev_tag;
+    if (dirty || prev) {
+        const uint4 c = make_uint4(key_colour(k01.x, pal), key_colour(k01.y, pal), key_colour(k23.x, pal),
+                                   key_colour(k23.y, pal));
+        __stcs(reinterpret_cast<uint4 *>(rgba) + q, c);
+    }
+    if (prev) {
+        const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
+        reinterpret_cast<ulonglong2 *>(next_keys)[2 * q] = e;
+        reinterpret_cast<ulonglong2 *>(next_keys)[2 * q + 1] = e;
+    }
+    if (dirty)
+        F.cur[chunk] = F.cur_tag;
 }
 
 // One frame of every cloud.  A point item copies its cloud's parameters from
@@ -167,7 +183,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTabl
     constexpr uint32_t G = Group<DT>::kPoints;
     __shared__ ItemParams sI;
     __shared__ uint32_t s_next, s_ok;
-    const int buf = *T.frame & 1;
+    const uint32_t frame = T.frame[0];
+    const uint32_t repaint = T.frame[1];
+    const int buf = frame & 1;
     if (threadIdx.x == 0)
         s_next = atomicAdd(T.next, 1u);
     __syncthreads();
@@ -192,8 +210,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTabl
                 const uint32_t quads = cl.npx / 4;
                 const uint32_t end = min(w.y + T.chunk_quads, quads);
                 const Palette pal{nullptr, nullptr, nullptr, 0u, cl.color, cl.background};
+                // frame numbers are the counter + 1, so the previous frame's is the counter; after a wrap
+                // old tags can only match too often, which costs stores, never a pixel
+                const FrameChunks F{cl.tags[buf ^ 1], cl.tags[buf], frame, frame + 1u, repaint};
                 for (uint32_t q = w.y + threadIdx.x; q < end; q += blockDim.x)
-                    resolve_quad_l2(keys, nk, cl.rgba, pal, q);
+                    resolve_quad_l2(keys, nk, cl.rgba, pal, q, F);
                 if (end == quads && quads * 4 + threadIdx.x < cl.npx) {     // the ragged tail
                     const uint32_t p = quads * 4 + threadIdx.x;
                     cl.rgba[p] = key_colour(__ldcg(keys + p), pal);
@@ -246,7 +267,12 @@ __global__ void batch_wait_selftest_kernel(const uint32_t *never_zero, uint32_t 
         wait_until_zero(never_zero, limit, err);
 }
 
-__global__ void batch_advance_kernel(uint32_t *frame) { *frame += 1u; }
+// After every frame: the next frame number, and no forced repaint.
+__global__ void batch_advance_kernel(uint32_t *frame)
+{
+    frame[0] += 1u;
+    frame[1] = 0u;
+}
 
 }  // namespace mmr
 
@@ -269,13 +295,16 @@ struct mmr_batch {
     void *pos_base = nullptr;
     unsigned long long *keys_base[2] = {nullptr, nullptr};
     uint32_t *rgba_base = nullptr;
+    uint32_t *tags_base = nullptr;       // chunk tags: [2][total_chunks]
+    std::vector<uint64_t> chunk_off;     // first chunk tag of each cloud
+    uint64_t total_chunks = 0;
     mmr::CloudDev *d_clouds = nullptr;
     mmr::Cam *d_cams = nullptr;
     uint2 *d_items = nullptr;        // work list in hand-out order
     uint64_t item_bytes = 0;
     uint32_t n_items = 0;
     int grid = 1;                    // resident CTAs of the persistent launch
-    uint32_t *d_frame = nullptr;
+    uint32_t *d_frame = nullptr;         // [0] frame counter, [1] repaint flag
     uint32_t *d_work = nullptr;      // [0] next item, [1] error bits, [2] self-test count (never zero)
     uint32_t *d_remaining = nullptr; // [count] unfinished point items per cloud, then [count] their full counts
     mmr::ItemParams *d_params = nullptr;
@@ -542,7 +571,8 @@ mmr_status mmr_batch_destroy(mmr_batch *b)
     bfree(b, (void **)&b->d_clouds, (uint64_t)b->count * sizeof(mmr::CloudDev));
     bfree(b, (void **)&b->d_cams, b->cams.size() * sizeof(mmr::Cam));
     bfree(b, (void **)&b->d_items, b->item_bytes);
-    bfree(b, (void **)&b->d_frame, 4);
+    bfree(b, (void **)&b->d_frame, 8);
+    bfree(b, (void **)&b->tags_base, 2 * 4 * b->total_chunks);
     bfree(b, (void **)&b->d_work, 3 * sizeof(uint32_t));
     bfree(b, (void **)&b->d_remaining, 2 * sizeof(uint32_t) * (uint64_t)b->count);
     bfree(b, (void **)&b->d_params, sizeof(mmr::ItemParams) * (uint64_t)b->count);
@@ -607,6 +637,8 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
         b->px_off.push_back(b->total_px);
         const uint64_t px = (uint64_t)clouds[c].width * clouds[c].height;
         b->total_px += (px + 31) / 32 * 32;             // keeps every framebuffer 256-byte aligned
+        b->chunk_off.push_back(b->total_chunks);
+        b->total_chunks += (px + 63) / 64;
     }
     b->cams.assign((size_t)camera_slots * count, mmr::Cam{});
     b->cam_set.assign((size_t)camera_slots * count, 0);
@@ -618,11 +650,13 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
     if (st == MMR_OK)
         st = balloc(b, (void **)&b->rgba_base, b->total_px * 4, "batch framebuffers");
     if (st == MMR_OK)
+        st = balloc(b, (void **)&b->tags_base, 2 * 4 * b->total_chunks, "batch chunk tags");
+    if (st == MMR_OK)
         st = balloc(b, (void **)&b->d_clouds, (uint64_t)count * sizeof(mmr::CloudDev), "cloud table");
     if (st == MMR_OK)
         st = balloc(b, (void **)&b->d_cams, b->cams.size() * sizeof(mmr::Cam), "camera table");
     if (st == MMR_OK)
-        st = balloc(b, (void **)&b->d_frame, 4, "frame counter");
+        st = balloc(b, (void **)&b->d_frame, 8, "frame counter and repaint flag");
     if (st == MMR_OK)
         st = balloc(b, (void **)&b->d_work, 3 * sizeof(uint32_t), "work counters");
     if (st == MMR_OK)
@@ -643,6 +677,8 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
             h.keys[0] = b->keys_base[0] + b->px_off[c];
             h.keys[1] = b->keys_base[1] + b->px_off[c];
             h.rgba = b->rgba_base + b->px_off[c];
+            h.tags[0] = b->tags_base + b->chunk_off[c];
+            h.tags[1] = b->tags_base + b->total_chunks + b->chunk_off[c];
             h.n = (uint32_t)d.n;
             h.npx = (uint32_t)((uint64_t)d.width * d.height);
             h.W = d.width;
@@ -668,7 +704,11 @@ mmr_status mmr_batch_create(int count, const mmr_cloud_desc *clouds, int dtype, 
         if (e == cudaSuccess)
             e = cudaMemset(b->rgba_base, 0, b->total_px * 4);
         if (e == cudaSuccess)
-            e = cudaMemset(b->d_frame, 0, 4);
+            e = cudaMemset(b->tags_base, 0, 2 * 4 * b->total_chunks);
+        if (e == cudaSuccess) {
+            const uint32_t fr[2] = {0u, 1u};        // frame 0, repaint everything
+            e = cudaMemcpy(b->d_frame, fr, sizeof fr, cudaMemcpyHostToDevice);
+        }
         if (e == cudaSuccess)
             e = cudaMallocHost((void **)&b->staging, b->cams.size() * sizeof(mmr::Cam));
         if (e == cudaSuccess)
@@ -938,8 +978,10 @@ mmr_status mmr_batch_autotune(mmr_batch *b, void *stream, int frames_per_config,
         re = cudaMemsetAsync(b->rgba_base, 0, b->total_px * 4, s);
     if (re == cudaSuccess)
         re = cudaStreamSynchronize(s);
-    if (re == cudaSuccess)
-        re = cudaMemcpy(b->d_frame, &saved_frames, 4, cudaMemcpyHostToDevice);
+    if (re == cudaSuccess) {
+        const uint32_t fr[2] = {saved_frames, 1u};   // the cleared buffers: the next frame repaints everything
+        re = cudaMemcpy(b->d_frame, fr, sizeof fr, cudaMemcpyHostToDevice);
+    }
     b->frames = saved_frames;
     bfree(b, &saved, b->pos_bytes);
     if (t0)

@@ -181,3 +181,45 @@ def test_batched_256_clouds_graph_sampled():
             assert np.array_equal(g[0], o[0]), f"positions of cloud {i} (n={c['n']})"
             assert np.array_equal(g[1], o[1]), f"keys of cloud {i}"
             assert np.array_equal(g[2], o[2]), f"rgba of cloud {i}"
+
+
+# (eye, target): the cloud in view, behind the camera (every point culled), from the side, partly in view
+_VIEWS = [((0.5, 0.5, 2.5), CENTRE), ((0.5, 0.5, -2.5), (0.5, 0.5, -5.0)), ((2.5, 0.5, 0.5), CENTRE),
+          ((0.5, 0.5, 2.5), (1.4, 1.3, 0.5))]
+
+
+@pytest.mark.parametrize("mode", ["direct", "graph", "roundtrip"])
+def test_batch_chunks_emptied_and_refilled(mode):
+    """The batch resolve repaints and clears only 64-pixel chunks that a frame
+    or the one before touched.  Each cloud's view turns away from it for a
+    frame and back (on different frames for different clouds), with non-zero
+    backgrounds and ragged frames; every cloud is compared with the oracle at
+    every frame."""
+    from paper_2504_20937_b300.api import Batch
+    sizes = [(20_000, 96, 64), (5_000, 61, 37), (30_000, 128, 128), (1_000, 7, 5)]
+    clouds, stored, _ = _make(sizes, "f32", seed=7)
+    frames = 2 * len(_VIEWS)
+    views = lambda f, i: _VIEWS[(f + i) % len(_VIEWS)]   # noqa: E731
+    with Batch(clouds, "f32", camera_slots=frames) as b:
+        _upload(b, stored)
+        for i in range(len(clouds)):
+            for f in range(frames):
+                eye, target = views(f, i)
+                b.set_camera(i, f, eye, target, UP, 60.0, 0.1, 100.0)
+        pos = [np.array(s, copy=True) for s in stored]
+        for f in range(frames):
+            if mode == "graph":
+                b.run_graph(1)
+            elif mode == "roundtrip":
+                b.step_and_render_roundtrip()
+            else:
+                b.step_and_render()
+            for i, c in enumerate(clouds):
+                oracle.displace(pos[i], "f32", c["seed"], c["cloud"], f, np.float32(c["amplitude"]))
+                eye, target = views(f, i)
+                M = oracle.camera_f32(eye, target, UP, 60.0, c["width"] / c["height"], 0.1, 100.0)
+                keys, rgba = oracle.render(pos[i], "f32", M, c["width"], c["height"], np.float32(0.1),
+                                           np.float32(100.0), None, c["color"], c["background"])
+                gpos, gk, gr = _download(b, i, "f32")
+                assert np.array_equal(gpos, pos[i]), (mode, f, i)
+                assert np.array_equal(gk, keys) and np.array_equal(gr, rgba), (mode, f, i)
