@@ -423,7 +423,8 @@ MMR_API mmr_status mmr_batch_device_bytes(const mmr_batch *b, uint64_t *bytes);
  *  - each viewer's private cloud is displaced (step = that viewer's frame
  *    index) and splatted into its own buffer, all viewers in one launch;
  *  - one resolve launch writes every viewer's RGBA8 frame: shared points in
- *    the shared colour, private points in the viewer's colour.
+ *    the shared colour, private points in the viewer's colour, storing only
+ *    in runs of 64 pixels that the view's frame or its previous one touched.
  * Point ids in the keys: shared point i -> i, private point j -> shared_n + j.
  * Viewers join and leave between ticks (continuous batching); a join whose
  * buffers would exceed the budget is refused with MMR_ERR_BUDGET and can be
@@ -448,7 +449,9 @@ MMR_API mmr_status mmr_serve_set_shared_color(mmr_serve *s, uint32_t color);
 /* Admit a viewer: private cloud of private_n points (zero-filled; write it
  * through mmr_serve_viewer_points before its first tick), a width x height
  * framebuffer, its own Philox key/cloud word/amplitude and colours.  Returns
- * the viewer id in *viewer.  MMR_ERR_BUDGET when its buffers do not fit
+ * the viewer id in *viewer.  A viewer needs 12 (FP32) or 6 bytes per private
+ * point (padded to 48-byte groups) and 20 bytes per pixel, plus 8 bytes per
+ * 64 pixels of chunk tags.  MMR_ERR_BUDGET when its buffers do not fit
  * beside those of the active viewers (nothing is allocated then).
  * shared_n + private_n must stay below 2^32.  Buffers kept from viewers
  * that left are reused when their size fits (a buffer at most twice the

@@ -52,6 +52,9 @@ struct ViewDev {
     float amplitude;
     uint32_t color, shared_color, background;
     uint32_t ph_a, ph_b, ph_c;      // prepared Philox words of the private cloud
+    const uint32_t *prev_tags;      // chunk tags of next_keys (FrameChunks), left by this view's previous frame
+    uint32_t *cur_tags;             // chunk tags of keys
+    uint32_t prev_tag, cur_tag;     // the view's previous and current frame numbers (frames rendered, + 1)
 };
 
 struct ServeTables {
@@ -189,14 +192,24 @@ __global__ void serve_resolve_kernel(ServeTables T)
                 return vw.background;
             return (uint32_t)(k & 0xffffffffu) < T.id_base ? vw.shared_color : vw.color;
         };
+        // colours and clears only in 64-pixel chunks this frame or the view's previous one touched, as in
+        // the single-cloud resolve (FrameChunks); a quad holding a key tags its chunk
         for (uint32_t q = ch.y + threadIdx.x; q < end; q += blockDim.x) {
             const ulonglong2 k01 = __ldcs(reinterpret_cast<const ulonglong2 *>(vw.keys) + 2 * q);
             const ulonglong2 k23 = __ldcs(reinterpret_cast<const ulonglong2 *>(vw.keys) + 2 * q + 1);
-            __stcs(reinterpret_cast<uint4 *>(vw.rgba) + q,
-                   make_uint4(colour(k01.x), colour(k01.y), colour(k23.x), colour(k23.y)));
-            const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
-            reinterpret_cast<ulonglong2 *>(vw.next_keys)[2 * q] = e;
-            reinterpret_cast<ulonglong2 *>(vw.next_keys)[2 * q + 1] = e;
+            const bool dirty = (k01.x & k01.y & k23.x & k23.y) != kEmptyKey;
+            const uint32_t chunk = q >> kChunkQuadShift;
+            const bool prev = __ldg(vw.prev_tags + chunk) == vw.prev_tag;
+            if (dirty || prev)
+                __stcs(reinterpret_cast<uint4 *>(vw.rgba) + q,
+                       make_uint4(colour(k01.x), colour(k01.y), colour(k23.x), colour(k23.y)));
+            if (prev) {
+                const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
+                reinterpret_cast<ulonglong2 *>(vw.next_keys)[2 * q] = e;
+                reinterpret_cast<ulonglong2 *>(vw.next_keys)[2 * q + 1] = e;
+            }
+            if (dirty)
+                vw.cur_tags[chunk] = vw.cur_tag;
         }
         if (end == quads && quads * 4 + threadIdx.x < vw.npx) {
             const uint32_t p = quads * 4 + threadIdx.x;
@@ -372,6 +385,16 @@ void vgive(mmr_serve *s, void **p, uint64_t *cap)
     *cap = 0;
 }
 
+// A viewer's depth-id buffers each end with the buffer's chunk tags, one
+// 32-bit word per 64 pixels; all zero at the join, which is what the first
+// frame (number 1) takes as its "previous frame", so it repaints everything.
+uint64_t tag_bytes(uint64_t npx) { return (npx + 63) / 64 * 4; }
+
+uint32_t *view_tags(const Viewer &v, int b)
+{
+    return reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(v.keys[b]) + (uint64_t)v.W * v.H * 8);
+}
+
 uint64_t padded_point_bytes(uint64_t n, int dtype)
 {
     const uint64_t raw = n * (dtype == MMR_F32x3 ? 12u : 6u);
@@ -413,6 +436,10 @@ mmr_status upload_tables(mmr_serve *S, cudaStream_t s, mmr::ServeTables &T)
         const int buf = (int)(v.frames & 1u);
         d.keys = v.keys[buf];
         d.next_keys = v.keys[buf ^ 1];
+        d.cur_tags = view_tags(v, buf);
+        d.prev_tags = view_tags(v, buf ^ 1);
+        d.cur_tag = v.frames + 1u;    // after a wrap old tags can only match too often: extra stores, same pixels
+        d.prev_tag = v.frames;
         d.rgba = v.rgba;
         d.pos = v.pos;
         d.n = (uint32_t)v.n;
@@ -680,7 +707,7 @@ mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int
     v.color = color;
     v.background = background;
     v.pos_bytes = padded_point_bytes(private_n, s->dtype);
-    v.bytes = v.pos_bytes + npx * 20;
+    v.bytes = v.pos_bytes + npx * 20 + 2 * tag_bytes(npx);
     const uint64_t in_use = s->held - s->cached;      // cached buffers can always be given up
     if (s->budget && in_use + v.bytes > s->budget)   // refuse before touching the allocator
         return sfail(s, MMR_ERR_BUDGET, "mmr_serve_add_viewer: %llu bytes would exceed the budget (%llu of %llu "
@@ -688,9 +715,9 @@ mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int
                      (unsigned long long)s->budget);
     mmr_status st = vtake(s, &v.pos, v.pos_bytes, &v.cap_pos, "private cloud");
     if (st == MMR_OK)
-        st = vtake(s, (void **)&v.keys[0], npx * 8, &v.cap_keys[0], "viewer depth-id buffer 0");
+        st = vtake(s, (void **)&v.keys[0], npx * 8 + tag_bytes(npx), &v.cap_keys[0], "viewer depth-id buffer 0");
     if (st == MMR_OK)
-        st = vtake(s, (void **)&v.keys[1], npx * 8, &v.cap_keys[1], "viewer depth-id buffer 1");
+        st = vtake(s, (void **)&v.keys[1], npx * 8 + tag_bytes(npx), &v.cap_keys[1], "viewer depth-id buffer 1");
     if (st == MMR_OK)
         st = vtake(s, (void **)&v.rgba, npx * 4, &v.cap_rgba, "viewer framebuffer");
     if (st == MMR_OK) {
@@ -701,6 +728,10 @@ mmr_status mmr_serve_add_viewer(mmr_serve *s, uint64_t private_n, int width, int
             e = cudaMemsetAsync(v.keys[0], 0xff, npx * 8, s->aux);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(v.keys[1], 0xff, npx * 8, s->aux);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(view_tags(v, 0), 0, tag_bytes(npx), s->aux);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(view_tags(v, 1), 0, tag_bytes(npx), s->aux);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(v.rgba, 0, npx * 4, s->aux);
         if (e == cudaSuccess)

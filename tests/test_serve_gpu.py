@@ -141,7 +141,7 @@ def test_serve_roundtrip_gives_same_frames():
 
 def test_serve_budget_admission_and_release():
     shared_bytes = (SHARED_N * 12 + 47) // 48 * 48
-    viewer_bytes = (1000 * 12 + 47) // 48 * 48 + 64 * 64 * 20
+    viewer_bytes = (1000 * 12 + 47) // 48 * 48 + 64 * 64 * 20 + 2 * 64 * 64 // 64 * 4   # + chunk tags
     with Server(SHARED_N, "f32", 1, 0, 1e-3, budget_bytes=shared_bytes + viewer_bytes + 100) as srv:
         a = srv.add_viewer(1000, 64, 64)
         assert srv.try_add_viewer(1000, 64, 64) is None          # refused, nothing allocated
@@ -293,7 +293,7 @@ def test_serve_reuses_departed_viewers_buffers():
     (its reused buffers were cleared), and a join that needs larger buffers
     makes the kept ones give way under a budget that holds one viewer."""
     shared_bytes = (SHARED_N * 12 + 47) // 48 * 48
-    budget = shared_bytes + (1000 * 12 + 47) // 48 * 48 + 64 * 64 * 20 + 100
+    budget = shared_bytes + (1000 * 12 + 47) // 48 * 48 + 64 * 64 * 20 + 2 * 64 * 64 // 64 * 4 + 100
     with Server(SHARED_N, "f32", SHARED_SEED, 0, float(AMP), budget_bytes=budget) as srv:
         srv.shared_points().copy_(torch.from_numpy(_shared()))
         srv.set_shared_color(SHARED_COLOR)
@@ -321,3 +321,47 @@ def test_serve_reuses_departed_viewers_buffers():
         assert srv.status()["device_bytes"] <= budget and srv.status()["active"] == 1
         want = _oracle_viewer_frame(2, 1000, 4097, 1, 3, 1, _eye(2, 0))
         assert np.array_equal(keys, want[0]) and np.array_equal(rgba, want[1])
+
+
+# (eye, target): the cloud in view, behind the camera (every point culled), from the side, partly in view
+_VIEWS = [((0.5, 0.5, 2.5), CEN), ((0.5, 0.5, -2.5), (0.5, 0.5, -5.0)), ((2.5, 0.5, 0.5), CEN),
+          ((0.5, 0.5, 2.5), (1.4, 1.3, 0.5))]
+
+
+@pytest.mark.parametrize("roundtrip", [False, True])
+def test_serve_chunks_emptied_and_refilled(roundtrip):
+    """The serving resolve stores only in 64-pixel chunks a view's frame or
+    its previous one touched.  Each viewer's view turns away for a tick and
+    back (on different ticks for different viewers), with non-zero
+    backgrounds and a ragged frame; every frame is compared with the oracle."""
+    specs = [(300, 64, 48), (2000, 61, 37), (50, 7, 5)]
+    ticks = 2 * len(_VIEWS)
+    view = lambda v, k: _VIEWS[(k + v) % len(_VIEWS)]   # noqa: E731
+    with Server(SHARED_N, "f32", SHARED_SEED, 0, float(AMP)) as srv:
+        srv.shared_points().copy_(torch.from_numpy(_shared()))
+        srv.set_shared_color(SHARED_COLOR)
+        ids = []
+        for v, (n, W, H) in enumerate(specs):
+            ids.append(srv.add_viewer(**_viewer_args(v, n, W, H)))
+            srv.viewer_points(ids[v]).copy_(torch.from_numpy(_private(v, n)))
+        shared = _shared()
+        priv = [_private(v, n) for v, (n, _, _) in enumerate(specs)]
+        for k in range(ticks):
+            for v, vid in enumerate(ids):
+                eye, target = view(v, k)
+                srv.set_camera(vid, eye, target, UP, 60.0, 0.1, 100.0)
+            srv.tick(roundtrip=roundtrip)
+            torch.cuda.synchronize()
+            oracle.displace_f32(shared, SHARED_SEED, 0, k, AMP)
+            for v, (n, W, H) in enumerate(specs):
+                oracle.displace_f32(priv[v], 3000 + v, 1 + v, k, AMP)
+                rgba, keys, f = srv.frame(ids[v])
+                assert f == k + 1
+                both = np.concatenate([shared, priv[v]])
+                colors = np.concatenate([np.full(SHARED_N, SHARED_COLOR, np.uint32),
+                                         np.full(n, 0xFF000000 | v, np.uint32)])
+                eye, target = view(v, k)
+                M = oracle.camera_f32(eye, target, UP, 60.0, W / H, 0.1, 100.0)
+                want = oracle.render(both, "f32", M, W, H, np.float32(0.1), np.float32(100.0), colors, 0, 0x10 + v)
+                assert np.array_equal(keys.cpu().numpy().reshape(-1).view(np.uint64), want[0]), (k, v)
+                assert np.array_equal(rgba.cpu().numpy().reshape(-1).view(np.uint32), want[1]), (k, v)
