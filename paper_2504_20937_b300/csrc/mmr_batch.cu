@@ -145,8 +145,7 @@ constexpr int kBatchMaxThreads = 512;
 // quad holding a key tags its chunk with this frame's number (lanes of a
 // warp storing the same tag to the same word make one store).
 __device__ __forceinline__ void resolve_quad_l2(const unsigned long long *keys, unsigned long long *next_keys,
-                                                uint32_t *rgba, const Palette &pal, uint32_t q,
-                                                const FrameChunks &F)
+                                                uint32_t *rgba, const Palette &pal, uint32_t q, FrameChunks F)
 {
     const ulonglong2 k01 = __ldcg(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q);
     const ulonglong2 k23 = __ldcg(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q + 1);
@@ -176,16 +175,18 @@ __device__ __forceinline__ void resolve_quad_l2(const unsigned long long *keys, 
 // thread building the parameters per item and the next item taken after the
 // current one: 0.770 -> 0.748 ms per frame.  The host round trip runs it twice
 // per frame: displace only (pixel items skipped), then render only from the
-// copied positions.
+// copied positions.  FP32 runs under a cap of 40 registers (8 bytes spilled;
+// uncapped the chunk bookkeeping of the pixel items takes it to 52): 0.606 ->
+// 0.587 ms per frame, tuned shape 256 threads, 8 CTAs per SM, 2048 groups per
+// item (a cap of 48: 0.591 ms).  The 16-bit bodies keep up to 64, as before.
+// Either cap, times kBatchMaxThreads threads, fits the register file.
 template <int DT, bool kDisplace, bool kSplat>
-__global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTables T)
+__global__ void __maxnreg__(DT == kF32 ? 40 : 64) batch_frame_kernel(BatchTables T)
 {
     constexpr uint32_t G = Group<DT>::kPoints;
     __shared__ ItemParams sI;
     __shared__ uint32_t s_next, s_ok;
-    const uint32_t frame = T.frame[0];
-    const uint32_t repaint = T.frame[1];
-    const int buf = frame & 1;
+    const int buf = *T.frame & 1;
     if (threadIdx.x == 0)
         s_next = atomicAdd(T.next, 1u);
     __syncthreads();
@@ -212,7 +213,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads) batch_frame_kernel(BatchTabl
                 const Palette pal{nullptr, nullptr, nullptr, 0u, cl.color, cl.background};
                 // frame numbers are the counter + 1, so the previous frame's is the counter; after a wrap
                 // old tags can only match too often, which costs stores, never a pixel
-                const FrameChunks F{cl.tags[buf ^ 1], cl.tags[buf], frame, frame + 1u, repaint};
+                const uint32_t frame = T.frame[0];
+                const FrameChunks F{cl.tags[buf ^ 1], cl.tags[buf], frame, frame + 1u, T.frame[1]};
+#pragma unroll 1
                 for (uint32_t q = w.y + threadIdx.x; q < end; q += blockDim.x)
                     resolve_quad_l2(keys, nk, cl.rgba, pal, q, F);
                 if (end == quads && quads * 4 + threadIdx.x < cl.npx) {     // the ragged tail
