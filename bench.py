@@ -107,7 +107,7 @@ def measured_peaks():
         return 6400.0, "fallback"
 
 
-_POINT_SOURCES = ("mmr_device.cuh", "mmr_kernels.cu", "mmr_points.cuh", "mmr_tiles.cuh")
+_POINT_SOURCES = ("mmr_device.cuh", "mmr_kernels.cu", "mmr_launch.cuh", "mmr_points.cuh", "mmr_tiles.cuh")
 KERNEL_SOURCES = {
     "points_kernel_f32_fused": _POINT_SOURCES,
     "points_kernel_f32_fused_depth_bound": _POINT_SOURCES,

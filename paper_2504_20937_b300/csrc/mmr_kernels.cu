@@ -1,6 +1,6 @@
 // Kernels of the single-cloud path: fused displace + project + splat over the
-// points (grid-stride over 48-byte point groups), and resolve + clear over
-// the pixels.
+// points (grid-stride over 48-byte point groups); the resolve is in
+// mmr_resolve.cu.
 #include <algorithm>
 #include <type_traits>
 
@@ -9,6 +9,7 @@
 #include "mmr_device.cuh"
 #include "mmr_disc.cuh"
 #include "mmr_internal.h"
+#include "mmr_launch.cuh"
 #include "mmr_points.cuh"
 #include "mmr_resolve.cuh"
 #include "mmr_tiles.cuh"
@@ -65,41 +66,6 @@ __device__ __forceinline__ void points_body(const void *src, void *dst, uint32_t
         }
         g = gn;
     }
-}
-
-// Every kernel of the frame loop (point kernels, resolve) is launched as a
-// programmatic dependent of the work before it on the stream (launch_dependent
-// below) and enters through this call.  The first instruction lets the next
-// dependent grid be scheduled while this one still runs; the second waits until
-// the preceding grid has completed and its writes are visible, before anything
-// is read or written.  Without a programmatic predecessor both return at once.
-__device__ __forceinline__ void enter_dependent_grid()
-{
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-// Launches a kernel that starts with enter_dependent_grid() with programmatic
-// stream serialization: its CTAs may be scheduled while the kernel before it on
-// the stream finishes, and it waits for that kernel's completion itself.
-// Measured on the 2^22-point 1920x1080 orbit: the resolve after the point
-// kernel 50.3 -> 48.9 us per flushed frame; the next frame's point kernel after
-// the resolve 45.1 -> 43.5 us per back-to-back frame.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), int grid, int threads, cudaStream_t s,
-                                    Args... args)
-{
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // FP32 storage.  Points are projected two at a time on packed FP32 pairs
@@ -451,51 +417,6 @@ cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cu
     return cudaGetLastError();
 }
 
-// Resolve + clear: four pixels per thread, whole warps grid-stride (a warp
-// takes 32 consecutive quads, two chunks); the ragged tail (npx not a
-// multiple of 4) goes to the first threads, always repainted and cleared.
-// Keys are read everywhere; colours are stored and the other buffer cleared
-// only in chunks that this frame or the previous one touched (FrameChunks).
-// Measured against repainting and clearing every pixel, same box: 2^22-point
-// 1920x1080 orbit 10.9 -> 8.9 us, 64M-point 16-cluster 3840x2160 frame
-// 22.9 -> 17.8 us, identical frames.
-__global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
-                               unsigned long long *__restrict__ next_keys,
-                               uint32_t *__restrict__ rgba, Palette pal, uint32_t npx, FrameChunks F)
-{
-    enter_dependent_grid();
-    const uint32_t quads = npx / 4;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t q0 = t - lane; q0 < quads; q0 += stride) {
-        const uint32_t q = q0 + lane;
-        bool dirty = false;
-        if (q < quads) {
-            const ulonglong2 k01 = __ldcs(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q);
-            const ulonglong2 k23 = __ldcs(reinterpret_cast<const ulonglong2 *>(keys) + 2 * q + 1);
-            dirty = (k01.x & k01.y & k23.x & k23.y) != kEmptyKey;
-            const bool prev = F.full || __ldg(F.prev + (q >> kChunkQuadShift)) == F.prev_tag;
-            if (dirty || prev) {
-                const uint4 c = make_uint4(key_colour(k01.x, pal), key_colour(k01.y, pal), key_colour(k23.x, pal),
-                                           key_colour(k23.y, pal));
-                __stcs(reinterpret_cast<uint4 *>(rgba) + q, c);
-            }
-            if (prev) {
-                const ulonglong2 e = make_ulonglong2(kEmptyKey, kEmptyKey);
-                reinterpret_cast<ulonglong2 *>(next_keys)[2 * q] = e;
-                reinterpret_cast<ulonglong2 *>(next_keys)[2 * q + 1] = e;
-            }
-        }
-        // lanes 0 and 16 tag their half-warp's chunk when any of its quads holds a key
-        const unsigned touched = __ballot_sync(0xffffffffu, dirty);
-        if ((lane & 15u) == 0 && ((touched >> lane) & 0xffffu) != 0)
-            F.cur[q >> kChunkQuadShift] = F.cur_tag;
-    }
-    if (quads * 4 + t < npx)
-        resolve_pixel(keys, next_keys, rgba, pal, quads * 4 + t);
-}
-
 // ---------------------------------------------------------------- launchers
 
 static int grid_for(uint64_t work_items, const LaunchShape &ls)
@@ -667,15 +588,6 @@ cudaError_t launch_points(int dtype, const void *src, void *dst, uint32_t n, con
     case kBF16: return launch_points_dt<kBF16>(src, dst, n, P, displace, splat, ls, s);
     default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
-                           const Palette &pal, uint32_t npx, const FrameChunks &F, cudaStream_t s)
-{
-    // pure streaming: one quad per thread, 256 threads, whatever the point kernel's shape.
-    const uint64_t quads = npx / 4;
-    const int grid = (int)std::max<uint64_t>(1, (quads + 255) / 256);
-    return launch_dependent(resolve_kernel, grid, 256, s, keys, next_keys, rgba, pal, npx, F);
 }
 
 }  // namespace mmr
