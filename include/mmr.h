@@ -405,7 +405,8 @@ MMR_API mmr_status mmr_batch_check_device(mmr_batch *b);
  * and no unbounded wait is involved. */
 MMR_API mmr_status mmr_batch_selftest_bounded_wait(mmr_batch *b, uint32_t max_polls, void *stream);
 
-/* Latest frame of one cloud (device pointers, as mmr_frame_ptr). */
+/* Latest frame of one cloud (device pointers, as mmr_frame_ptr; read-only to
+ * the caller for the same reason). */
 MMR_API mmr_status mmr_batch_frame_ptr(mmr_batch *b, int cloud, const uint32_t **rgba,
                                        const uint64_t **depth_id);
 
@@ -479,7 +480,9 @@ MMR_API mmr_status mmr_serve_remove_viewer(mmr_serve *s, int viewer);
 MMR_API mmr_status mmr_serve_tick(mmr_serve *s, void *stream);
 MMR_API mmr_status mmr_serve_tick_roundtrip(mmr_serve *s, void *stream);
 
-/* Latest frame of a viewer (device pointers) and how many frames it has had. */
+/* Latest frame of a viewer (device pointers) and how many frames it has had.
+ * Read-only to the caller, as for mmr_frame_ptr: each resolve repaints only
+ * the runs of 64 pixels that the view's frame or its previous one touched. */
 MMR_API mmr_status mmr_serve_frame_ptr(mmr_serve *s, int viewer, const uint32_t **rgba, const uint64_t **depth_id,
                                        uint32_t *frame_index);
 
