@@ -307,6 +307,28 @@ MMR_API mmr_status mmr_selftest_bounded_wait(mmr_ctx *ctx, long long max_cycles,
 /* Device bytes this context holds right now. */
 MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
 
+/* Host mirror of the framebuffer: width*height RGBA8 pixels (uint32, row 0
+ * at the top) of pinned host memory that the context allocates, mapped into
+ * the device's address space, and frees in mmr_destroy.  A host counterpart
+ * of the paper's display reading the latest frame (Sec. 1): instead of
+ * copying the whole framebuffer to the host every frame, mmr_mirror_frame
+ * enqueues on `stream` a kernel that writes over the host link only the runs
+ * of 64 pixels that differ from what the mirror holds (those the latest
+ * frame touched, and those where the mirror still holds a point of an
+ * earlier frame; everything after the mirror is allocated or the background
+ * colour changes).  Once `stream` is synchronised the mirror equals the
+ * latest frame.  The stream may differ from the one that renders: the next
+ * frame's resolve waits for the kernel (the resolve rewrites the device
+ * framebuffer the kernel reads), so the copy overlaps the next point phase.
+ * Frames may be skipped; the mirror catches up at the next call.  The host
+ * must not read the mirror while a mmr_mirror_frame is in flight.
+ * mmr_mirror_bytes reports the bytes written to the mirror since it was
+ * allocated (synchronises the device).  MMR_ERR_STATE before the mirror
+ * exists or before the first frame. */
+MMR_API mmr_status mmr_alloc_host_mirror(mmr_ctx *ctx, uint32_t **host_rgba);
+MMR_API mmr_status mmr_mirror_frame(mmr_ctx *ctx, void *stream);
+MMR_API mmr_status mmr_mirror_bytes(mmr_ctx *ctx, uint64_t *bytes);
+
 /* ---- batched clouds --------------------------------------------------------
  * Many independent clouds, each with its own size, framebuffer, camera and
  * displacement parameters, advanced and rendered together by one persistent

@@ -65,6 +65,9 @@ SIGNATURES = {
     "mmr_selftest_bounded_wait": (_i, [_vp, C.c_longlong, _vp]),
     "mmr_last_kernel_ms": (_i, [_vp, C.POINTER(_f), C.POINTER(_f)]),
     "mmr_device_bytes": (_i, [_vp, C.POINTER(_u64)]),
+    "mmr_alloc_host_mirror": (_i, [_vp, C.POINTER(_vp)]),
+    "mmr_mirror_frame": (_i, [_vp, _vp]),
+    "mmr_mirror_bytes": (_i, [_vp, C.POINTER(_u64)]),
 }
 
 

@@ -237,6 +237,27 @@ class Context:
         self._check(self._lib.mmr_device_bytes(self._h, C.byref(b)))
         return b.value
 
+    def alloc_host_mirror(self):
+        """numpy uint32[H, W] view of the library's host mirror of the
+        framebuffer (pinned host memory); mirror_frame keeps it current."""
+        import numpy as np
+        p = C.c_void_p()
+        self._check(self._lib.mmr_alloc_host_mirror(self._h, C.byref(p)))
+        buf = (C.c_uint32 * (self.W * self.H)).from_address(p.value)
+        self._mirror = np.ctypeslib.as_array(buf).reshape(self.H, self.W)
+        return self._mirror
+
+    def mirror_frame(self, stream=None):
+        """Enqueue the update of the host mirror to the latest frame on
+        `stream` (only the 64-pixel runs that changed cross the host link)."""
+        self._check(self._lib.mmr_mirror_frame(self._h, stream_handle(stream)))
+
+    def mirror_bytes(self) -> int:
+        """Bytes written to the host mirror since it was allocated."""
+        b = C.c_uint64()
+        self._check(self._lib.mmr_mirror_bytes(self._h, C.byref(b)))
+        return b.value
+
 
 class Batch:
     """Many independent clouds advanced and rendered together (mmr_batch_*).

@@ -40,6 +40,16 @@ struct mmr_ctx {
     uint32_t buf_frame[2] = {0, 0};   // number of the frame last resolved from each depth-id buffer
     bool repaint_all = true;      // the next resolve repaints and clears every pixel
 
+    // host mirror of the framebuffer (mmr_alloc_host_mirror): mapped pinned host memory, and on the device one
+    // byte per chunk (does the mirror hold a point there) after an 8-byte count of the bytes written
+    uint32_t *mirror = nullptr;           // host pointer
+    uint32_t *mirror_dev = nullptr;       // its device alias
+    unsigned char *mirror_mem = nullptr;  // count, then the chunk bytes
+    bool mirror_full = true;              // the next mirror update writes every pixel
+    bool mirror_pending = false;          // a mirror update may still read the framebuffer
+    cudaEvent_t frame_done = nullptr;     // recorded after every resolve once the mirror exists
+    cudaEvent_t mirror_done = nullptr;    // recorded after every mirror update
+
     void *buf[2] = {nullptr, nullptr};   // point buffers; buf[1] only with ping-pong
     int visible = 0;                     // the buffer holding the current state (rendered)
     uint64_t n = 0;
@@ -232,6 +242,24 @@ void frame_resolved(mmr_ctx *c, int cur)
     c->repaint_all = false;
 }
 
+uint64_t mirror_mem_bytes(const mmr_ctx *c) { return 8 + frame_chunks_of(c); }
+
+// Before a resolve on s: a mirror update still reading the framebuffer it
+// rewrites must finish first.
+cudaError_t before_resolve(mmr_ctx *c, cudaStream_t s)
+{
+    if (!c->mirror_pending)
+        return cudaSuccess;
+    c->mirror_pending = false;
+    return cudaStreamWaitEvent(s, c->mirror_done, 0);
+}
+
+// After a resolve on s: the point a mirror update on another stream waits for.
+cudaError_t after_resolve(mmr_ctx *c, cudaStream_t s)
+{
+    return c->mirror ? cudaEventRecord(c->frame_done, s) : cudaSuccess;
+}
+
 // The depth-bound path pays for disc markers where many discs cover each
 // pixel: at least kDiscCoverMin on average (n pi r^2 / pixels), for clouds of
 // at least 2^20 points.  Measured on the 2^22-point 1080p orbit (direct ->
@@ -377,7 +405,11 @@ mmr_status frame(mmr_ctx *c, const void *src, void *dst, bool displace, cudaStre
     const int cur = c->splat_buf;
     const mmr::FrameChunks F = frame_chunks(c, cur, s, &e);
     if (e == cudaSuccess)
+        e = before_resolve(c, s);
+    if (e == cudaSuccess)
         e = mmr::launch_resolve(c->keys[cur], c->keys[cur ^ 1], c->rgba, palette(c), (uint32_t)frame_px(c), F, s);
+    if (e == cudaSuccess)
+        e = after_resolve(c, s);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "resolve kernel launch");
     frame_resolved(c, cur);
@@ -552,6 +584,13 @@ mmr_status mmr_destroy(mmr_ctx *ctx)
         else
             free(ctx->rt_host);
     }
+    dev_free(ctx, (void **)&ctx->mirror_mem, mirror_mem_bytes(ctx));
+    if (ctx->mirror)
+        cudaFreeHost(ctx->mirror);
+    if (ctx->frame_done)
+        cudaEventDestroy(ctx->frame_done);
+    if (ctx->mirror_done)
+        cudaEventDestroy(ctx->mirror_done);
     if (ctx->ring) {
         for (uint32_t k = 0; k < 3 * kTimingRing; ++k)
             if (ctx->ring[k])
@@ -712,8 +751,12 @@ mmr_status mmr_nbody_step_and_render(mmr_ctx *ctx, float G, float eps2, float dt
     const int cur = ctx->splat_buf;
     const mmr::FrameChunks F = frame_chunks(ctx, cur, s, &e);
     if (e == cudaSuccess)
+        e = before_resolve(ctx, s);
+    if (e == cudaSuccess)
         e = mmr::launch_resolve(ctx->keys[cur], ctx->keys[cur ^ 1], ctx->rgba, palette(ctx), (uint32_t)frame_px(ctx),
                                 F, s);
+    if (e == cudaSuccess)
+        e = after_resolve(ctx, s);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e, "resolve kernel launch");
     frame_resolved(ctx, cur);
@@ -842,8 +885,10 @@ mmr_status mmr_set_style(mmr_ctx *ctx, uint32_t color, uint32_t background)
     if (!ctx)
         return MMR_ERR_INVALID_ARG;
     ctx->color = color;
-    if (background != ctx->background)
+    if (background != ctx->background) {
         ctx->repaint_all = true;      // pixels left as background by earlier frames are repainted
+        ctx->mirror_full = true;      // and so are those of the host mirror
+    }
     ctx->background = background;
     return MMR_OK;
 }
@@ -1090,6 +1135,96 @@ mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes)
     if (!ctx || !bytes)
         return MMR_ERR_INVALID_ARG;
     *bytes = ctx->held;
+    return MMR_OK;
+}
+
+mmr_status mmr_alloc_host_mirror(mmr_ctx *ctx, uint32_t **host_rgba)
+{
+    if (!ctx || !host_rgba)
+        return MMR_ERR_INVALID_ARG;
+    if (ctx->mirror) {
+        *host_rgba = ctx->mirror;
+        return MMR_OK;
+    }
+    *host_rgba = nullptr;
+    mmr_status st = dev_alloc(ctx, (void **)&ctx->mirror_mem, mirror_mem_bytes(ctx), "host mirror chunk state");
+    if (st != MMR_OK)
+        return st;
+    void *h = nullptr, *d = nullptr;
+    cudaError_t e = cudaMemset(ctx->mirror_mem, 0, mirror_mem_bytes(ctx));
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&h, frame_px(ctx) * 4, cudaHostAllocMapped);
+    if (e == cudaSuccess)
+        e = cudaHostGetDevicePointer(&d, h, 0);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ctx->frame_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&ctx->mirror_done, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h)
+            cudaFreeHost(h);
+        if (ctx->frame_done)
+            cudaEventDestroy(ctx->frame_done);
+        if (ctx->mirror_done)
+            cudaEventDestroy(ctx->mirror_done);
+        ctx->frame_done = ctx->mirror_done = nullptr;
+        dev_free(ctx, (void **)&ctx->mirror_mem, mirror_mem_bytes(ctx));
+        return cuda_fail(ctx, e, "mmr_alloc_host_mirror");
+    }
+    memset(h, 0, frame_px(ctx) * 4);
+    ctx->mirror = static_cast<uint32_t *>(h);
+    ctx->mirror_dev = static_cast<uint32_t *>(d);
+    ctx->mirror_full = true;
+    ctx->mirror_pending = false;
+    *host_rgba = ctx->mirror;
+    return MMR_OK;
+}
+
+mmr_status mmr_mirror_frame(mmr_ctx *ctx, void *stream)
+{
+    mmr::NvtxRange nvtx("mmr_mirror_frame");
+    if (!ctx)
+        return MMR_ERR_INVALID_ARG;
+    if (!ctx->mirror)
+        return fail(ctx, MMR_ERR_STATE, "mmr_mirror_frame: no host mirror (call mmr_alloc_host_mirror first)");
+    if (ctx->frame_no == 0)
+        return fail(ctx, MMR_ERR_STATE, "mmr_mirror_frame: no frame rendered yet");
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int latest = ctx->latest_buf;
+    // resolves record frame_done only once the mirror exists, so the update that fills the whole mirror (the
+    // first one, or the first after a background change) synchronises with the device instead of waiting on it
+    cudaError_t e = cudaSuccess;
+    if (ctx->mirror_full)
+        e = cudaDeviceSynchronize();
+    else
+        e = cudaStreamWaitEvent(s, ctx->frame_done, 0);
+    if (e == cudaSuccess)
+        e = mmr::launch_mirror(ctx->rgba, ctx->mirror_dev, (uint32_t)frame_px(ctx), ctx->chunk_tags[latest],
+                               ctx->buf_frame[latest], ctx->mirror_mem + 8, ctx->mirror_full ? 1 : 0,
+                               reinterpret_cast<unsigned long long *>(ctx->mirror_mem), s);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(ctx->mirror_done, s);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_mirror_frame");
+    ctx->mirror_full = false;
+    ctx->mirror_pending = true;
+    return MMR_OK;
+}
+
+mmr_status mmr_mirror_bytes(mmr_ctx *ctx, uint64_t *bytes)
+{
+    if (!ctx || !bytes)
+        return MMR_ERR_INVALID_ARG;
+    if (!ctx->mirror)
+        return fail(ctx, MMR_ERR_STATE, "mmr_mirror_bytes: no host mirror");
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpy(&v, ctx->mirror_mem, 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "mmr_mirror_bytes");
+    *bytes = v;
     return MMR_OK;
 }
 

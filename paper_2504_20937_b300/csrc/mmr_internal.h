@@ -74,6 +74,14 @@ cudaError_t launch_bounded_wait_selftest(long long max_cycles, uint32_t *err, cu
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
                            const Palette &pal, uint32_t npx, const FrameChunks &F, cudaStream_t s);
 
+// Host mirror: write into `host` (mapped pinned memory, npx uint32) the quads
+// of every 64-pixel chunk the frame numbered `tag` touched (chunk tags
+// `tags`) or the mirror still holds a point in (`held`, one byte per chunk,
+// updated), or of every chunk when `full`; the ragged tail pixels always.
+// Adds the bytes written to *bytes.
+cudaError_t launch_mirror(const uint32_t *rgba, uint32_t *host, uint32_t npx, const uint32_t *tags, uint32_t tag,
+                          unsigned char *held, int full, unsigned long long *bytes, cudaStream_t s);
+
 // Displacement amplitudes the kernels accept: 0, or [2^-100, 1] (so that
 // amplitude * 2^-23 is a normal float and the scaling is exact).
 inline bool amplitude_ok(float a) { return a == 0.0f || (a >= 0x1p-100f && a <= 1.0f); }

@@ -57,6 +57,54 @@ __global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
         resolve_pixel(keys, next_keys, rgba, pal, quads * 4 + t);
 }
 
+// Host mirror update: whole warps over 32 consecutive quads (two chunks, as
+// in the resolve).  A chunk is copied when the latest frame tagged it or the
+// mirror still holds a point there (held), and then held becomes "tagged":
+// what the mirror holds afterwards.  Every lane of a half warp reads held
+// before its first lane rewrites it.  Stores to the mapped host memory are
+// 16 bytes per lane, 512 contiguous bytes per warp.
+__global__ void mirror_kernel(const uint32_t *__restrict__ rgba, uint32_t *__restrict__ host, uint32_t npx,
+                              const uint32_t *__restrict__ tags, uint32_t tag, unsigned char *__restrict__ held,
+                              int full, unsigned long long *bytes)
+{
+    const uint32_t quads = npx / 4;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t copied = 0;
+    for (uint32_t q0 = t - lane; q0 < quads; q0 += stride) {
+        const uint32_t q = q0 + lane;
+        const uint32_t chunk = q >> kChunkQuadShift;
+        bool touched = false, copy = false;
+        if (q < quads) {
+            touched = tags[chunk] == tag;
+            copy = full || touched || held[chunk] != 0;
+            if (copy)
+                reinterpret_cast<uint4 *>(host)[q] = __ldcs(reinterpret_cast<const uint4 *>(rgba) + q);
+        }
+        __syncwarp();
+        if ((lane & 15u) == 0 && q < quads)
+            held[chunk] = touched ? 1 : 0;
+        copied += copy ? 16u : 0u;
+    }
+    if (quads * 4 + t < npx) {
+        host[quads * 4 + t] = rgba[quads * 4 + t];
+        copied += 4u;
+    }
+    copied = __reduce_add_sync(0xffffffffu, copied);
+    if (lane == 0 && copied)
+        atomicAdd(bytes, (unsigned long long)copied);
+}
+
+cudaError_t launch_mirror(const uint32_t *rgba, uint32_t *host, uint32_t npx, const uint32_t *tags, uint32_t tag,
+                          unsigned char *held, int full, unsigned long long *bytes, cudaStream_t s)
+{
+    const uint64_t quads = npx / 4;
+    const int grid = (int)std::max<uint64_t>(1, (quads + 255) / 256);
+    mirror_kernel<<<grid, 256, 0, s>>>(rgba, host, npx, tags, tag, held, full, bytes);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_resolve(const unsigned long long *keys, unsigned long long *next_keys, uint32_t *rgba,
                            const Palette &pal, uint32_t npx, const FrameChunks &F, cudaStream_t s)
 {
