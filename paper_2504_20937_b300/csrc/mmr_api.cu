@@ -1197,10 +1197,13 @@ mmr_status mmr_mirror_frame(mmr_ctx *ctx, void *stream)
     // resolves record frame_done only once the mirror exists, so the update that fills the whole mirror (the
     // first one, or the first after a background change) synchronises with the device instead of waiting on it
     cudaError_t e = cudaSuccess;
-    if (ctx->mirror_full)
+    if (ctx->mirror_full) {
         e = cudaDeviceSynchronize();
-    else
+    } else {
         e = cudaStreamWaitEvent(s, ctx->frame_done, 0);
+        if (e == cudaSuccess && ctx->mirror_pending)      // updates run one after another (they share `held`)
+            e = cudaStreamWaitEvent(s, ctx->mirror_done, 0);
+    }
     if (e == cudaSuccess)
         e = mmr::launch_mirror(ctx->rgba, ctx->mirror_dev, (uint32_t)frame_px(ctx), ctx->chunk_tags[latest],
                                ctx->buf_frame[latest], ctx->mirror_mem + 8, ctx->mirror_full ? 1 : 0,
