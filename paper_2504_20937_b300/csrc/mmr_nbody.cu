@@ -28,11 +28,50 @@ namespace mmr {
 constexpr uint32_t kNbodyChunk = 1024;
 constexpr int kNbodyTile = 128;
 
+// One term t_j, in the fixed order above.
+__device__ __forceinline__ void nbody_term(float4 b, float px, float py, float pz, float eps2, float &tx, float &ty,
+                                           float &tz)
+{
+    const float dx = __fsub_rn(b.x, px);
+    const float dy = __fsub_rn(b.y, py);
+    const float dz = __fsub_rn(b.z, pz);
+    const float r2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)), eps2);
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(r2));
+    const float s = __fmul_rn(b.w, __fmul_rn(__fmul_rn(inv, inv), inv));
+    tx = __fmul_rn(dx, s);
+    ty = __fmul_rn(dy, s);
+    tz = __fmul_rn(dz, s);
+}
+
+// Terms of bodies a and b (two consecutive j) at once on packed FP32 pairs:
+// every element is the IEEE operation of nbody_term (subtraction as the
+// addition of the exact negation; each product that feeds an addition an
+// fma with -0, so the assembler cannot fuse it); the square root and the
+// division stay scalar.
+__device__ __forceinline__ void nbody_term_pair(float4 a, float4 b, F2 NPX, F2 NPY, F2 NPZ, F2 EPS2, float &txa,
+                                                float &tya, float &tza, float &txb, float &tyb, float &tzb)
+{
+    const F2 DX = f2_add(f2(a.x, b.x), NPX);
+    const F2 DY = f2_add(f2(a.y, b.y), NPY);
+    const F2 DZ = f2_add(f2(a.z, b.z), NPZ);
+    const F2 R2 = f2_add(f2_add(f2_add(f2_product(DX, DX), f2_product(DY, DY)), f2_product(DZ, DZ)), EPS2);
+    float ra, rb;
+    f2_split(R2, ra, rb);
+    const F2 INV = f2(__fdiv_rn(1.0f, __fsqrt_rn(ra)), __fdiv_rn(1.0f, __fsqrt_rn(rb)));
+    const F2 S = f2_mul(f2(a.w, b.w), f2_mul(f2_mul(INV, INV), INV));
+    f2_split(f2_product(DX, S), txa, txb);
+    f2_split(f2_product(DY, S), tya, tyb);
+    f2_split(f2_product(DZ, S), tza, tzb);
+}
+
+// Each tile holds (x, y, z, m) of kNbodyTile bodies, so a term reads one
+// 16-byte word of shared memory.  Terms are computed two at a time
+// (nbody_term_pair) and added to the sums one after another in j order.
 __global__ void __launch_bounds__(kNbodyTile) nbody_partial_kernel(const float *__restrict__ pin,
                                                                    const float *__restrict__ mass, uint32_t n,
                                                                    float eps2, float4 *__restrict__ partial)
 {
-    __shared__ float tx[kNbodyTile], ty[kNbodyTile], tz[kNbodyTile], tm[kNbodyTile];
+    __shared__ float4 tile[kNbodyTile];
     const uint32_t i = blockIdx.x * kNbodyTile + threadIdx.x;
     const uint32_t c0 = blockIdx.y * kNbodyChunk;
     const uint32_t c1 = min(c0 + kNbodyChunk, n);
@@ -42,30 +81,30 @@ __global__ void __launch_bounds__(kNbodyTile) nbody_partial_kernel(const float *
         py = pin[3ull * i + 1];
         pz = pin[3ull * i + 2];
     }
+    const F2 NPX = f2(-px, -px), NPY = f2(-py, -py), NPZ = f2(-pz, -pz), EPS2 = f2(eps2, eps2);
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;
     for (uint32_t t = c0; t < c1; t += kNbodyTile) {
         const uint32_t j = t + threadIdx.x;
-        if (j < c1) {
-            tx[threadIdx.x] = pin[3ull * j];
-            ty[threadIdx.x] = pin[3ull * j + 1];
-            tz[threadIdx.x] = pin[3ull * j + 2];
-            tm[threadIdx.x] = mass[j];
-        }
+        if (j < c1)
+            tile[threadIdx.x] = make_float4(pin[3ull * j], pin[3ull * j + 1], pin[3ull * j + 2], mass[j]);
         __syncthreads();
         const uint32_t cnt = min((uint32_t)kNbodyTile, c1 - t);
         if (i < n) {
-#pragma unroll 4
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const float dx = __fsub_rn(tx[k], px);
-                const float dy = __fsub_rn(ty[k], py);
-                const float dz = __fsub_rn(tz[k], pz);
-                const float r2 = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
-                                                     __fmul_rn(dz, dz)), eps2);
-                const float inv = __fdiv_rn(1.0f, __fsqrt_rn(r2));
-                const float s = __fmul_rn(tm[k], __fmul_rn(__fmul_rn(inv, inv), inv));
-                sx = __fadd_rn(sx, __fmul_rn(dx, s));
-                sy = __fadd_rn(sy, __fmul_rn(dy, s));
-                sz = __fadd_rn(sz, __fmul_rn(dz, s));
+            uint32_t k = 0;
+#pragma unroll 2
+            for (; k + 1 < cnt; k += 2) {
+                float txa, tya, tza, txb, tyb, tzb;
+                nbody_term_pair(tile[k], tile[k + 1], NPX, NPY, NPZ, EPS2, txa, tya, tza, txb, tyb, tzb);
+                sx = __fadd_rn(__fadd_rn(sx, txa), txb);
+                sy = __fadd_rn(__fadd_rn(sy, tya), tyb);
+                sz = __fadd_rn(__fadd_rn(sz, tza), tzb);
+            }
+            if (k < cnt) {
+                float tx, ty, tz;
+                nbody_term(tile[k], px, py, pz, eps2, tx, ty, tz);
+                sx = __fadd_rn(sx, tx);
+                sy = __fadd_rn(sy, ty);
+                sz = __fadd_rn(sz, tz);
             }
         }
         __syncthreads();
