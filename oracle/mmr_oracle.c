@@ -97,6 +97,9 @@ static float uniform24_f32(uint32_t r)
     return (float)(r >> 8) * 0x1p-24f;   /* exact: a 24-bit integer times 2^-24 */
 }
 
+/* The clamp to [0, 1] takes IEEE 754 maxNum / minNum (C's fmaxf / fminf):
+ * +inf -> 1, -inf -> 0, and a NaN coordinate, which only a caller's own NaN
+ * input can produce, -> 0, so every coordinate stays in the unit box.       */
 static float move_axis_f32(float p, uint32_t r, float a)
 {
     float u = uniform24_f32(r);
@@ -104,9 +107,7 @@ static float move_axis_f32(float p, uint32_t r, float a)
     t = t + (-1.0f);
     float d = a * t;
     float q = p + d;
-    if (q < 0.0f) q = 0.0f;
-    if (q > 1.0f) q = 1.0f;
-    return q;
+    return fminf(fmaxf(q, 0.0f), 1.0f);
 }
 
 void orc_displace_f32(float *pos, uint64_t n, uint64_t seed, uint32_t cloud, uint32_t step, float a)

@@ -119,6 +119,20 @@ def test_displacement_invariants_and_clamp():
     assert (pos == 0.0).sum() > 0 and (pos == 1.0).sum() > 0
 
 
+def test_displacement_clamps_non_finite_and_out_of_box_inputs():
+    """Reading 3 (clamp) on inputs a caller may write: NaN and -inf go to 0,
+    +inf and anything that stays above 1 after the step to 1, anything below
+    0 to 0; an in-box coordinate moves by at most a.  The same with a = 0:
+    the clamp still applies."""
+    vals = np.array([np.nan, np.inf, -np.inf, 1e30, -1e30, 2.0, -2.0, 0.5], np.float32)
+    want = np.array([0, 1, 0, 1, 0, 1, 0], np.float32)
+    for a in (np.float32(0.0), np.float32(1e-3)):
+        pos = np.repeat(vals[:, None], 3, axis=1)
+        oracle.displace_f32(pos, 9, 0, 0, a)
+        assert np.array_equal(pos[:7], np.repeat(want[:, None], 3, axis=1)), a
+        assert np.all(np.abs(pos[7] - np.float32(0.5)) <= a), a
+
+
 def test_displacement_fp32_within_rounding_bound_of_fp64():
     """Each FP32 step rounds twice (a*t and p+d), each at most half an ulp of a
     value below 1 + a, so after s steps |p32 - p64| <= s (1 + a) 2^-24."""
