@@ -320,8 +320,10 @@ MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
  * latest frame.  The stream may differ from the one that renders: the next
  * frame's resolve waits for the kernel (the resolve rewrites the device
  * framebuffer the kernel reads), so the copy overlaps the next point phase.
- * Frames may be skipped; the mirror catches up at the next call.  The host
- * must not read the mirror while a mmr_mirror_frame is in flight.
+ * Frames may be skipped; the mirror catches up at the next call.  An update
+ * that writes every pixel (the first, and the first after a background
+ * change) synchronises the device before it is enqueued.  The host must not
+ * read the mirror while a mmr_mirror_frame is in flight.
  * mmr_mirror_bytes reports the bytes written to the mirror since it was
  * allocated (synchronises the device).  MMR_ERR_STATE before the mirror
  * exists or before the first frame. */
