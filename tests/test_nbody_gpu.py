@@ -19,7 +19,7 @@ CEN = (0.5, 0.5, 0.5)
 UP = (0.0, 1.0, 0.0)
 
 
-@pytest.mark.parametrize("n", [1, 255, 257, 1025, 3001])
+@pytest.mark.parametrize("n", [1, 2, 3, 127, 128, 129, 255, 257, 1023, 1024, 1025, 2049, 3001])
 def test_nbody_steps_bit_exact(n):
     W, H, steps = 96, 64, 3
     G, eps2, dt = np.float32(2e-4), np.float32(1e-3), np.float32(5e-2)
