@@ -29,8 +29,9 @@ VIEWS = [((0.5, 0.5, 2.5), CENTRE), ((0.5, 0.5, -2.5), (0.5, 0.5, -5.0)), ((2.5,
          ((0.5, 0.5, 2.5), (1.4, 1.3, 0.5)), ((0.5, 0.5, 2.5), CENTRE)]
 
 
-def _frames(stored, dtype, W, H, views, styles, seed=5, amplitude=1e-3):
-    """GPU and oracle frames for a sequence of views and (colour, background) styles."""
+def _frames(stored, dtype, W, H, views, styles, seed=5, amplitude=1e-3, launches=None):
+    """GPU and oracle frames for a sequence of views and (colour, background)
+    styles; launches, if given, is each frame's (kernel, threads, CTAs per SM)."""
     n = stored.shape[0]
     got, want = [], []
     pos = np.array(stored, copy=True)
@@ -39,6 +40,9 @@ def _frames(stored, dtype, W, H, views, styles, seed=5, amplitude=1e-3):
         upload(ctx, stored)
         ctx.set_sim(seed, 0, amplitude, 0)
         for f, ((eye, target), (color, bg)) in enumerate(zip(views, styles)):
+            if launches is not None:
+                kernel, threads, ctas = launches[f]
+                ctx.set_launch(threads, ctas, kernel)
             ctx.set_style(color, bg)
             ctx.set_camera(eye, target, UP, 60.0, 0.1, 100.0)
             ctx.step_and_render()
@@ -112,3 +116,35 @@ def test_frame_ptr_buffers_after_empty_frame():
         assert (got[f][0] == np.uint64(2**64 - 1)).all() and (got[f][1] == 0x01020304).all()
     _assert_frames(got, want, "empty frames")
     torch.cuda.synchronize()
+
+
+# per frame: (kernel, threads, CTAs per SM): grid-stride with one thread per
+# group and persistent, the two-pass depth bounds, the warp-aggregated splat
+# and the TMA-staged kernel, in turn.
+SWITCHES = [("grid", 64, 0), ("depth_bound", 64, 0), ("grid", 64, 0), ("warp_agg", 64, 0), ("tma", 256, 1),
+            ("grid", 128, 2), ("grid", 64, 0), ("depth_bound", 64, 0), ("grid", 64, 0)]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_kernel_switches_between_frames(dtype):
+    """A different point kernel each frame, with views that empty and refill
+    chunks: the chunk bookkeeping holds whichever kernel filled the buffer,
+    and every frame equals the oracle."""
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(60_003, 65, components=3, sigma=0.05), dtype)
+    views = [VIEWS[0], VIEWS[2], VIEWS[1], VIEWS[3], VIEWS[0], VIEWS[1], VIEWS[2], VIEWS[0], VIEWS[3]]
+    got, want = _frames(stored, dtype, 97, 61, views, [(0xFFFFFFFF, 0x10203040)] * len(views), launches=SWITCHES)
+    _assert_frames(got, want, f"kernel switches {dtype}")
+
+
+@pytest.mark.parametrize("dtype,n", [("f32", 1), ("f32", 3), ("f32", 7), ("f16", 5), ("f16", 13)])
+def test_ragged_tail_chunks(dtype, n):
+    """Clouds of a few points, all or some of them in the ragged last group
+    (fewer than 4 FP32 or 8 16-bit points), which a single thread splats
+    outside the vector path: the few chunks those points fill are repainted
+    and cleared as they come and go.  Frames of 61x37 and 64x64 pixels."""
+    stored = inputs.encode(inputs.uniform_cloud(n, 66 + n), dtype)
+    views = [VIEWS[0], VIEWS[0], VIEWS[1], VIEWS[0], VIEWS[2]]
+    for W, H in [(61, 37), (64, 64)]:
+        got, want = _frames(stored, dtype, W, H, views, [(0xFFFFFFFF, 0x01020304)] * len(views), amplitude=1e-2)
+        assert any((gk != np.uint64(2**64 - 1)).any() for gk, _ in got)
+        _assert_frames(got, want, f"{n} points {dtype} {W}x{H}")
