@@ -416,7 +416,7 @@ def run_ours(args, rank, world, local):
                       "d2h_bytes_per_step": mirror_bytes, "frames": e2e_frames,
                       "mirror_equals_device_frame": mirror_ok,
                       "note": "camera matrix in as kernel parameters; every frame delivered to the library's "
-                              "host mirror of the framebuffer (mmr_mirror_frame on a second stream: only the "
+                              "host mirror of the framebuffer (mmr_mirror_frame on a second, high-priority stream: only the "
                               "64-pixel runs that changed since the mirror's last update cross the host link, "
                               "overlapping the next frame's point phase); d2h bytes counted by the library; all "
                               "updates complete inside the timed region; the mirror's first, whole-frame fill "
@@ -490,12 +490,13 @@ def storage_accuracy(make_ctx, sc, pos64, dtype):
 def e2e_mirror(ctx, sc, frames, stream):
     """Seconds for `frames` frames through the public API, each with its
     camera set and the library's host mirror brought up to it by
-    mmr_mirror_frame on a second stream; the loop ends when the last update
+    mmr_mirror_frame on a second stream of the highest priority; the loop ends when the last update
     has landed.  Returns (seconds, d2h bytes per frame as counted by the
     library, whether the mirror then equals the device framebuffer)."""
     import torch
     mirror = ctx.alloc_host_mirror()
-    copy_stream = torch.cuda.Stream()
+    # the update's CTAs go ahead of the next frame's point kernel (include/mmr.h)
+    copy_stream = torch.cuda.Stream(priority=torch.cuda.Stream.priority_range()[1])
     ctx.set_camera(sc.eye(0), CENTRE, UP, sc.fovy_deg, sc.znear, sc.zfar)
     ctx.step_and_render(stream)
     ctx.mirror_frame(copy_stream)             # the first update fills the whole mirror

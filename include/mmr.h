@@ -320,7 +320,11 @@ MMR_API mmr_status mmr_device_bytes(const mmr_ctx *ctx, uint64_t *bytes);
  * latest frame.  The stream may differ from the one that renders: the next
  * frame's resolve waits for the kernel (the resolve rewrites the device
  * framebuffer the kernel reads), so the copy overlaps the next point phase.
- * Frames may be skipped; the mirror catches up at the next call.  An update
+ * Give that stream a higher priority than the rendering stream: the kernel's
+ * CTAs then start ahead of the next point kernel's instead of after them, and
+ * the next resolve does not wait for them (measured on a 3840x2160 frame of
+ * 2^26 points: 10 us added per frame instead of 40 us).  Frames may be
+ * skipped; the mirror catches up at the next call.  An update
  * that writes every pixel (the first, and the first after a background
  * change) synchronises the device before it is enqueued.  The host must not
  * read the mirror while a mmr_mirror_frame is in flight.

@@ -57,36 +57,52 @@ __global__ void resolve_kernel(const unsigned long long *__restrict__ keys,
         resolve_pixel(keys, next_keys, rgba, pal, quads * 4 + t);
 }
 
-// Host mirror update: whole warps over 32 consecutive quads (two chunks, as
-// in the resolve).  A chunk is copied when the latest frame tagged it or the
-// mirror still holds a point there (held), and then held becomes "tagged":
-// what the mirror holds afterwards.  Every lane of a half warp reads held
-// before its first lane rewrites it.  Stores to the mapped host memory are
-// 16 bytes per lane, 512 contiguous bytes per warp.
+// Host mirror update, one lane per chunk: a warp reads the tags and `held`
+// bytes of 32 consecutive chunks (one coalesced access each), decides which
+// to copy (the latest frame tagged it, or the mirror still holds a point
+// there: held) and sets held to "tagged", what the mirror holds afterwards;
+// then the whole warp copies the chosen chunks, two at a time, 16 lanes of
+// 16 bytes on each 256-byte chunk.  The pixels past the last whole quad
+// (npx not a multiple of 4) are left out of the chunk tags by the resolve, so
+// they are copied every time.  A warp adds the bytes it wrote to *bytes.
 __global__ void mirror_kernel(const uint32_t *__restrict__ rgba, uint32_t *__restrict__ host, uint32_t npx,
                               const uint32_t *__restrict__ tags, uint32_t tag, unsigned char *__restrict__ held,
                               int full, unsigned long long *bytes)
 {
     const uint32_t quads = npx / 4;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t chunks = (quads + 15) / 16;      // chunks holding at least one whole quad
     const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     uint32_t copied = 0;
-    for (uint32_t q0 = t - lane; q0 < quads; q0 += stride) {
-        const uint32_t q = q0 + lane;
-        const uint32_t chunk = q >> kChunkQuadShift;
-        bool touched = false, copy = false;
-        if (q < quads) {
-            touched = tags[chunk] == tag;
-            copy = full || touched || held[chunk] != 0;
-            if (copy)
-                reinterpret_cast<uint4 *>(host)[q] = __ldcs(reinterpret_cast<const uint4 *>(rgba) + q);
+    for (uint32_t c0 = warp * 32; c0 < chunks; c0 += warps * 32) {
+        const uint32_t c = c0 + lane;
+        bool copy = false;
+        if (c < chunks) {
+            const bool touched = tags[c] == tag;
+            copy = full || touched || held[c] != 0;
+            held[c] = touched ? 1 : 0;
         }
-        __syncwarp();
-        if ((lane & 15u) == 0 && q < quads)
-            held[chunk] = touched ? 1 : 0;
-        copied += copy ? 16u : 0u;
+        unsigned todo = __ballot_sync(0xffffffffu, copy);
+        while (todo) {
+            const uint32_t a = __ffs(todo) - 1;
+            todo &= todo - 1;
+            uint32_t b = 32;
+            if (todo) {
+                b = __ffs(todo) - 1;
+                todo &= todo - 1;
+            }
+            const uint32_t mine = lane < 16 ? a : b;
+            if (mine < 32) {
+                const uint32_t q = (c0 + mine) * 16 + (lane & 15u);
+                if (q < quads) {
+                    reinterpret_cast<uint4 *>(host)[q] = __ldcs(reinterpret_cast<const uint4 *>(rgba) + q);
+                    copied += 16u;
+                }
+            }
+        }
     }
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (quads * 4 + t < npx) {
         host[quads * 4 + t] = rgba[quads * 4 + t];
         copied += 4u;
@@ -99,8 +115,9 @@ __global__ void mirror_kernel(const uint32_t *__restrict__ rgba, uint32_t *__res
 cudaError_t launch_mirror(const uint32_t *rgba, uint32_t *host, uint32_t npx, const uint32_t *tags, uint32_t tag,
                           unsigned char *held, int full, unsigned long long *bytes, cudaStream_t s)
 {
-    const uint64_t quads = npx / 4;
-    const int grid = (int)std::max<uint64_t>(1, (quads + 255) / 256);
+    // one warp per 32 chunks, 256 threads per block
+    const uint64_t chunks = ((uint64_t)npx / 4 + 15) / 16;
+    const int grid = (int)std::max<uint64_t>(1, (chunks + 255) / 256);
     mirror_kernel<<<grid, 256, 0, s>>>(rgba, host, npx, tags, tag, held, full, bytes);
     return cudaGetLastError();
 }
