@@ -10,6 +10,8 @@
 
 Mirrors the paper's usage model (Mimir, Listing 1 and Table 2): the
 visualised allocation comes from the library and is written in place.
+Every view handed out (points, framebuffer, keys, host mirror) aliases
+memory the context owns: it must not be used after close().
 """
 from __future__ import annotations
 
