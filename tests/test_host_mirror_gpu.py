@@ -39,7 +39,7 @@ def _context(stored, W, H, seed=5, amplitude=1e-3):
     return ctx
 
 
-@pytest.mark.parametrize("W,H", [(160, 96), (61, 37), (3, 3), (1, 1)])
+@pytest.mark.parametrize("W,H", [(160, 96), (61, 37), (3, 3), (1, 1), (1001, 333)])
 def test_mirror_follows_every_frame(W, H):
     stored = inputs.encode(inputs.gaussian_mixture_cloud(40_003, 71, components=3, sigma=0.05), "f32")
     views = VIEWS * 3
@@ -60,15 +60,18 @@ def test_mirror_follows_every_frame(W, H):
             assert np.array_equal(got, want[f]), f"mirror frame {f}"
 
 
-def test_mirror_skipped_frames_and_no_host_sync_between():
-    """Render on one stream and update the mirror on another every third
-    frame, with no host synchronisation until the end of each group of
-    frames; the next frame's resolve waits for the update in flight."""
+@pytest.mark.parametrize("side_priority", ["default", "highest"])
+def test_mirror_skipped_frames_and_no_host_sync_between(side_priority):
+    """Render on one stream and update the mirror on another (of the default
+    or the highest priority) every third frame, with no host synchronisation
+    until the end of each group of frames; the next frame's resolve waits
+    for the update in flight."""
     W, H = 128, 80
     stored = inputs.encode(inputs.gaussian_mixture_cloud(60_000, 72, components=4, sigma=0.04), "f32")
     views = VIEWS * 6
     want = _oracle_frames(stored, W, H, views, [0] * len(views))
-    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    prio = torch.cuda.Stream.priority_range()[1] if side_priority == "highest" else 0
+    main, side = torch.cuda.Stream(), torch.cuda.Stream(priority=prio)
     with _context(stored, W, H) as ctx:
         mirror = ctx.alloc_host_mirror()
         for f, (eye, target) in enumerate(views):
@@ -109,6 +112,42 @@ def test_mirror_bytes_only_changes_cross():
         assert ctx.mirror_bytes() == W * H * 4 + 2 * touched_runs * 256
         torch.cuda.synchronize()
         assert (mirror == 0).all()
+
+
+def test_mirror_bytes_ragged_frame():
+    """On a frame whose pixel count is a multiple of neither 4 nor 64 an
+    update writes 16 bytes for every whole quad of each run it copies (runs
+    holding a key in a whole quad, plus those the mirror still holds a point
+    in) and the last 1-3 pixels every time."""
+    W, H = 1001, 333
+    npx, quads = W * H, W * H // 4
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(30_000, 75, components=2, sigma=0.02), "f32")
+
+    def runs_holding_keys(keys):
+        held = (keys[:4 * quads].reshape(quads, 4) != np.uint64(2**64 - 1)).any(axis=1)
+        return set(np.unique(np.nonzero(held)[0] // 16).tolist())
+
+    def run_bytes(runs):
+        return sum(16 * (min(quads, 16 * (r + 1)) - 16 * r) for r in runs)
+
+    with _context(stored, W, H, amplitude=0.0) as ctx:
+        ctx.alloc_host_mirror()
+        ctx.set_camera(*VIEWS[0], UP, 60.0, 0.1, 100.0)
+        ctx.step_and_render()
+        ctx.mirror_frame()
+        assert ctx.mirror_bytes() == 16 * quads + 4 * (npx % 4)
+        total = ctx.mirror_bytes()
+        held = runs_holding_keys(ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64))
+        assert held
+        for eye_target in (VIEWS[3], VIEWS[1], VIEWS[1], VIEWS[0]):
+            ctx.set_camera(*eye_target, UP, 60.0, 0.1, 100.0)
+            ctx.step_and_render()
+            ctx.mirror_frame()
+            now = runs_holding_keys(ctx.frame_keys().cpu().numpy().reshape(-1).view(np.uint64))
+            total += run_bytes(now | held) + 4 * (npx % 4)
+            assert ctx.mirror_bytes() == total
+            held = now
+        torch.cuda.synchronize()
 
 
 def test_mirror_state_errors():
