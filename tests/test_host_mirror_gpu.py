@@ -150,6 +150,32 @@ def test_mirror_bytes_ragged_frame():
         torch.cuda.synchronize()
 
 
+def test_mirror_4k_frame():
+    """A 3840x2160 frame of a 16-cluster cloud on an orbit, the mirror brought
+    up to date after every frame on a stream of the highest priority: equal to
+    the oracle's frame each time, with only the changed runs written after the
+    first update."""
+    W, H = 3840, 2160
+    stored = inputs.encode(inputs.gaussian_mixture_cloud(1 << 20, 76), "f32")
+    frames = 4
+    eyes = [inputs.orbit_eye(f, 3.0) for f in range(frames)]
+    side = torch.cuda.Stream(priority=torch.cuda.Stream.priority_range()[1])
+    pos = stored.copy()
+    with _context(stored, W, H, amplitude=5e-4) as ctx:
+        mirror = ctx.alloc_host_mirror()
+        for f, eye in enumerate(eyes):
+            ctx.set_camera(eye, CENTRE, UP, 60.0, 0.1, 100.0)
+            ctx.step_and_render()
+            ctx.mirror_frame(side)
+            side.synchronize()
+            oracle.displace(pos, "f32", 5, 0, f, np.float32(5e-4))
+            M = oracle.camera_f32(eye, CENTRE, UP, 60.0, W / H, 0.1, 100.0)
+            _, want = oracle.render(pos, "f32", M, W, H, np.float32(0.1), np.float32(100.0))
+            assert np.array_equal(mirror.reshape(-1), want), f"mirror frame {f}"
+        assert ctx.mirror_bytes() < W * H * 4 * 2       # the first update writes the frame, the others far less
+        torch.cuda.synchronize()
+
+
 def test_mirror_state_errors():
     stored = inputs.encode(inputs.uniform_cloud(1000, 74), "f32")
     with _context(stored, 32, 32) as ctx:
